@@ -1,0 +1,246 @@
+/*
+ * superpoint.h -- C ABI of the GB300 super point detection library.
+ *
+ * The library implements the data-parallel path of the SLGA scheme of
+ * Xu, Ding and Hu, "Most memory efficient distributed super points detection
+ * on core networks" (arXiv 1901.07306):
+ *
+ *   scan      every <hip, oip> pair sets bits in the short estimator array
+ *             vector (SEAV, Sec. 3.1-3.2) and the long estimator array
+ *             (LDCA, Sec. 3.3) of one watch point (WP, Sec. 4.1);
+ *   merge     the WPs' sketches are combined into the global ones (Sec. 4.2);
+ *   detect    hot SEs -> candidate index sets -> SEU test -> LP/IP
+ *             reconstruction (Eq. 3) -> LDCA union filter (Eq. 4), Sec. 3.2-3.3.
+ *
+ * Conventions shared by every call:
+ *   - A pair stream is an array of uint32_t, two per pair: element 2j is the
+ *     monitored host hip (source IP), element 2j+1 its opposite IP oip
+ *     (Def. 1).  Addresses are plain host-order 32-bit integers.
+ *   - "dev_" pointers are CUDA device pointers of the current device;
+ *     "host_" pointers are host memory (pinned memory gives overlapped
+ *     copies, pageable memory works but copies synchronously).
+ *   - All GPU work of a context is issued on the context's stream.  Calls
+ *     marked "async" return once the work is enqueued; the caller keeps
+ *     inputs alive until the stream has passed that work.
+ *   - Every call returns SP_OK (0), a positive warning, or a negative error
+ *     code; sp_strerror() names it.  No call aborts the process.
+ *   - The library owns all sketch, staging and scratch memory of a context;
+ *     it is allocated in sp_create() and released by sp_destroy().
+ *   - A context is not thread safe: one host thread at a time.
+ */
+#ifndef SUPERPOINT_H
+#define SUPERPOINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SP_API __attribute__((visibility("default")))
+#else
+#define SP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define SP_OK 0
+#define SP_WARN_THETA_BELOW_INIT 1   /* detect threshold < params.theta (see sp_detect_async) */
+#define SP_ERR_PARAM (-1)            /* invalid argument or parameter set */
+#define SP_ERR_ROUTER (-2)           /* router index out of range */
+#define SP_ERR_TRUNCATED (-3)        /* more results than the caller's cap; first cap written */
+#define SP_ERR_CANDIDATE_OVERFLOW (-4) /* device result or join bound exceeded; list incomplete */
+#define SP_ERR_CUDA (-5)             /* a CUDA runtime call failed */
+#define SP_ERR_TIMEOUT (-6)          /* a bounded wait gave up */
+#define SP_ERR_CHECKSUM (-7)         /* imported sketch image is corrupt or mismatched */
+#define SP_ERR_NOMEM (-8)            /* device or host allocation failed */
+#define SP_ERR_STATE (-9)            /* call not valid in the context's current state */
+
+/* sp_candidate.flags */
+#define SP_FLAG_SATURATED 1u         /* z0 == 0: the LDC union is full; est = k ln k */
+
+/*
+ * Parameters (Sec. 3.1-3.3; defaults by sp_default_params()).
+ *
+ * SEAV (Sec. 3.2): 2^r SEAs selected by RP = the low r bits of hip; each SEA
+ * has sr rows, row i holding SC(i) = 2^ibn[i] one-byte SEs (g = 8 bits,
+ * Sec. 3.1) indexed by Idx(i, LP) (Eq. 2) with LP = hip >> r.  The rows must
+ * cover every LP bit (Sec. 3.2 constraint 1) and row i must share at least one
+ * LP bit with row (i + 1) mod sr (constraint 2, read as an overlap).  Library
+ * limits: r <= 24, 1 <= sr <= 8, 1 <= ibn[i] <= 12, isb[i] < 32 - r, and the
+ * bytes of one SEA (sum of SC(i)) at most 4096.
+ *
+ * LDCA (Sec. 3.3): lr rows x 2^lc_log2 columns of LDCs of k = 2^k_log2 bits;
+ * 5 <= k_log2 <= 16, 1 <= lr <= 8, lc_log2 <= 24, lr * 2^lc_log2 * k <= 2^32.
+ *
+ * theta fixes the SE sampling level tau = ceil(log2(theta / 8)) (Eq. 1) at
+ * scan time; theta >= 1.
+ *
+ * n_routers sketches (one per simulated watch point) are held by the context.
+ * window_slices = 1 is the discrete window of Sec. 3; > 1 selects the sliding
+ * window of Sec. 5 over that many time slices (see sp_slide).
+ * max_candidates bounds the detect result buffer (0 = 1 << 20).
+ * max_join bounds the LPs that reach the LDCA test in one detect (0 = 1 << 26).
+ * seed seeds the hash family: multiply-add-shift hashes whose (a, b) words are
+ * consecutive SplitMix64 outputs for H1, H3, LH_0 .. LH_{lr-1}.
+ */
+typedef struct sp_params {
+  uint32_t r;
+  uint32_t sr;
+  uint32_t isb[8];
+  uint32_t ibn[8];
+  uint32_t k_log2;
+  uint32_t lr;
+  uint32_t lc_log2;
+  uint32_t theta;
+  uint32_t n_routers;
+  uint32_t window_slices;
+  uint32_t max_candidates;
+  uint32_t reserved0;
+  uint64_t seed;
+  uint64_t max_join;
+} sp_params;
+
+/* One detected super point (Def. 2 via Sec. 3.2-3.3).  z0 = zero bits of the
+ * host's LDC union; est = -k ln(z0 / k) (Eq. 4), k ln k when saturated. */
+typedef struct sp_candidate {
+  uint32_t ip;
+  uint32_t z0;
+  double est;
+  uint32_t flags;
+  uint32_t pad;
+} sp_candidate;
+
+typedef struct sp_ctx sp_ctx;
+
+/* Fills *out with the default profile: r = 14, sr = 4, isb = {0, 5, 10, 15},
+ * ibn = 7 (the Sec. 3.2 rule IBN = ceil(L / SR) + a, ISB(i) = i ceil(L / SR)
+ * with L = 18, a = 2), k = 1024, lr = 4, LC = 2^16, theta = 1024, one router,
+ * discrete window.  SEAV = 8 MiB, LDCA = 32 MiB. */
+SP_API int sp_default_params(sp_params* out);
+
+/* Validates *p against the Sec. 3.2 constraints and the library limits above.
+ * Returns SP_OK or SP_ERR_PARAM. */
+SP_API int sp_check_params(const sp_params* p);
+
+/* Bytes of one router's SEAV and LDCA for *p (the logical layout that
+ * sp_export writes).  Either output may be NULL. */
+SP_API int sp_sketch_bytes(const sp_params* p, uint64_t* seav_bytes, uint64_t* ldca_bytes);
+
+/* tau of Eq. 1 and Z_theta = max{ z in [0, k] : -k ln(z / k) >= threshold }
+ * (Eq. 4 as an integer test), as the library computes them. */
+SP_API uint32_t sp_tau(uint32_t theta);
+SP_API uint32_t sp_z_theta(uint32_t k_log2, uint32_t threshold);
+
+/* Creates a context on the current CUDA device.  cuda_stream is a
+ * cudaStream_t (NULL = the legacy default stream); the context issues all
+ * its work there.  Allocates and zeroes n_routers sketches plus scratch.
+ * Errors: SP_ERR_PARAM, SP_ERR_NOMEM, SP_ERR_CUDA.  *out is NULL on error. */
+SP_API int sp_create(const sp_params* p, void* cuda_stream, sp_ctx** out);
+
+/* Releases every resource of ctx after draining its stream.  NULL is a no-op. */
+SP_API void sp_destroy(sp_ctx* ctx);
+
+/* Replaces the context's stream (work already issued stays ordered on the old
+ * one; the caller synchronises if needed). */
+SP_API int sp_set_stream(sp_ctx* ctx, void* cuda_stream);
+
+/* Copy of the parameters the context was created with. */
+SP_API int sp_get_params(const sp_ctx* ctx, sp_params* out);
+
+/* Starts a new discrete window for one router (Sec. 3: every bit is 0 at the
+ * beginning of a time period): zeroes its SEAV and LDCA.  Async.
+ * In a sliding context it also forgets every slice.  Errors: SP_ERR_ROUTER. */
+SP_API int sp_reset(sp_ctx* ctx, uint32_t router);
+
+/* Scan (Sec. 3.1-3.3, Sec. 4.1): for every pair of dev_pairs[0 .. 2 n_pairs),
+ * sets bit H2(oip) of the SE at Idx(i, LP(hip)) in every row i of SEA RP(hip)
+ * when lsb(H1(oip)) >= tau, and bit H3(oip) of LDC LH_i(hip) in every LDCA
+ * row i.  dev_pairs is borrowed until the stream passes the work; it must be
+ * 8-byte aligned.  n_pairs = 0 is a no-op.  Bit setting is idempotent and
+ * order independent (Sec. 3.4), so updates may be split arbitrarily.
+ * In a sliding context the bits are stamped with the current slice.  Async.
+ * Errors: SP_ERR_ROUTER, SP_ERR_PARAM (NULL or misaligned pointer), SP_ERR_CUDA. */
+SP_API int sp_update(sp_ctx* ctx, uint32_t router, const uint32_t* dev_pairs, uint64_t n_pairs);
+
+/* The watch point's host path of Sec. 4.1: host_pairs are copied to the GPU
+ * in fixed-size chunks through two device staging buffers, the copy of chunk
+ * j + 1 overlapping the scan of chunk j.  Returns when every chunk is
+ * enqueued; host_pairs must stay valid until the stream has passed them.
+ * Same semantics and errors as sp_update. */
+SP_API int sp_update_host(sp_ctx* ctx, uint32_t router, const uint32_t* host_pairs, uint64_t n_pairs);
+
+/* Batched scan: n_batches (router, pairs, n_pairs) triples of device streams
+ * of uneven sizes are scanned by one persistent launch.  routers[b] may
+ * repeat.  The three arrays are host arrays of n_batches entries.  Async.
+ * Same per-batch semantics and errors as sp_update. */
+SP_API int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
+                      const uint32_t* const* dev_pairs, const uint64_t* n_pairs);
+
+/* Global SEAV/LDCA of Sec. 4.2: dst |= src for every source router, bitwise
+ * OR over both structures (the OR of the WPs' sketches equals the sketch of
+ * the union of their streams).  routers is a host array of n indices; it may
+ * contain dst_router.  Async.  Errors: SP_ERR_ROUTER, SP_ERR_PARAM. */
+SP_API int sp_merge(sp_ctx* ctx, const uint32_t* routers, uint32_t n, uint32_t dst_router);
+
+/* Restore + filter (Sec. 3.2-3.3) on one router's sketch, enqueued on the
+ * stream: HSE(i) = SEs of weight >= 3; every candidate index set of the
+ * cartesian product whose rows agree on their shared LP bits and whose SEU
+ * (AND of the chosen SEs) has weight >= 3 gives LP by Eq. 3 and
+ * ip = LP << r | RP; ip is kept when the AND of its LDCs over all LDCA rows has
+ * z0 <= Z_theta(threshold) zero bits.  Results are sorted by ascending ip and
+ * stay on the device until sp_results().  threshold 0 means params.theta.
+ * Returns SP_WARN_THETA_BELOW_INIT when threshold < params.theta (tau, and so
+ * the SE sensitivity, was fixed at scan time).  Errors: SP_ERR_ROUTER,
+ * SP_ERR_CUDA. */
+SP_API int sp_detect_async(sp_ctx* ctx, uint32_t router, uint32_t threshold);
+
+/* Waits for the stream, then copies the last detect's results:
+ * *n_total = number of super points found; min(*n_total, cap) records go to
+ * host_out (may be NULL when cap = 0).  Errors: SP_ERR_TRUNCATED when
+ * *n_total > cap; SP_ERR_CANDIDATE_OVERFLOW when the device result buffer
+ * (max_candidates) or the join bound (max_join) overflowed, in which case the
+ * list is incomplete; SP_ERR_STATE when no detect was issued; SP_ERR_CUDA. */
+SP_API int sp_results(sp_ctx* ctx, sp_candidate* host_out, uint64_t cap, uint64_t* n_total);
+
+/* sp_detect_async followed by sp_results. */
+SP_API int sp_detect(sp_ctx* ctx, uint32_t router, uint32_t threshold,
+              sp_candidate* host_out, uint64_t cap, uint64_t* n_total);
+
+/* Device view of the last detect's sorted results (valid until the next
+ * detect): *dev_records points at max_candidates sp_candidate slots,
+ * *dev_count at the uint32 count of valid ones (which may exceed
+ * max_candidates on overflow).  No synchronisation. */
+SP_API int sp_results_device(sp_ctx* ctx, const sp_candidate** dev_records, const uint32_t** dev_count);
+
+/* Sliding window (Sec. 5): closes the current time slice of a sliding
+ * context and opens the next; bits last set more than window_slices - 1
+ * slices ago become inactive ("0") for detect.  Async.  In a discrete
+ * context (window_slices = 1) it equals sp_reset.  Errors: SP_ERR_ROUTER. */
+SP_API int sp_slide(sp_ctx* ctx, uint32_t router);
+
+/* Checkpoint / WP->GS shipment (Sec. 4.2): a self-describing image of one
+ * router's sketch in the logical layout -- header, SEAV bytes
+ * [2^r][sum SC(i)], LDCA words [lr][LC][k / 32] (bit b of an LDC is bit
+ * b % 32 of word b / 32) -- followed by a 64-bit checksum.  With host_buf NULL
+ * *n receives the image size.  Synchronises the stream.
+ * Errors: SP_ERR_TRUNCATED (cap too small), SP_ERR_ROUTER, SP_ERR_CUDA. */
+SP_API int sp_export(sp_ctx* ctx, uint32_t router, void* host_buf, uint64_t cap, uint64_t* n);
+
+/* Loads an image written by sp_export into a router, replacing its sketch.
+ * Rejects an image with a bad checksum or parameters other than the
+ * context's (SP_ERR_CHECKSUM) without touching the router. */
+SP_API int sp_import(sp_ctx* ctx, uint32_t router, const void* host_buf, uint64_t n);
+
+/* Human-readable name of a status code (static storage). */
+SP_API const char* sp_strerror(int code);
+
+/* Library version as MAJOR * 10000 + MINOR * 100 + PATCH. */
+SP_API int sp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SUPERPOINT_H */

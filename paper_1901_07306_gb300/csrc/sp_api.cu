@@ -1,0 +1,502 @@
+// sp_api.cu -- host side of the C ABI declared in include/superpoint.h.
+//
+// Owns the per-context device memory (n_routers sketches, detect scratch,
+// staging buffers for the host path), validates parameters against Sec. 3.2's
+// constraints, derives the hash words from the seed, and enqueues the kernels
+// of sp_scan.cu, sp_merge.cu and sp_detect.cu on the context's stream.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "sp_internal.h"
+
+using sp::DetectStatus;
+using sp::DevParams;
+
+namespace {
+
+constexpr uint64_t kDefaultMaxCandidates = 1ull << 20;
+constexpr uint64_t kDefaultMaxJoin = 1ull << 26;
+constexpr uint64_t kStagingPairs = 1ull << 22;      // 32 MiB per staging buffer
+constexpr uint64_t kAlign = 256;
+
+uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// SplitMix64 (Steele, Lea, Flood 2014).
+uint64_t splitmix64_next(uint64_t* s) {
+  uint64_t z = (*s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+bool row_covers(uint32_t isb, uint32_t ibn, uint32_t L, uint32_t bit) {
+  // is LP bit `bit` one of isb, isb + 1, ..., isb + ibn - 1 (mod L)?
+  const uint32_t d = (bit + L - isb) % L;
+  return d < ibn;
+}
+
+uint64_t sea_bytes_of(const sp_params* p) {
+  uint64_t s = 0;
+  for (uint32_t i = 0; i < p->sr; ++i) s += 1ull << p->ibn[i];
+  return s;
+}
+
+uint32_t log2_ceil_u64(uint64_t x) {
+  uint32_t b = 0;
+  while ((1ull << b) < x) ++b;
+  return b;
+}
+
+// 64-bit FNV-1a over bytes.
+uint64_t fnv1a64(const void* data, uint64_t n, uint64_t h = 0xCBF29CE484222325ull) {
+  const uint8_t* p = static_cast<const uint8_t*>(data);
+  for (uint64_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 0x100000001B3ull;
+  }
+  return h;
+}
+
+struct ImageHeader {
+  char magic[8];             // "SPSKETCH"
+  uint32_t version;          // 1
+  uint32_t header_bytes;     // sizeof(ImageHeader)
+  uint32_t r, sr, isb[8], ibn[8], k_log2, lr, lc_log2, theta;
+  uint64_t seed;
+  uint64_t seav_bytes, ldca_bytes;
+};
+
+}  // namespace
+
+struct sp_ctx {
+  sp_params p;
+  DevParams d;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int scan_grid = 0;
+  uint64_t seav_bytes = 0, ldca_bytes = 0, seav_pad = 0, stride = 0;
+  uint8_t* sketches = nullptr;              // n_routers * stride bytes
+  uint64_t* keys = nullptr;                 // detect scratch: next_pow2(cap) keys
+  sp_candidate* records = nullptr;          // sorted results, cap records
+  DetectStatus* status = nullptr;
+  double* est_table = nullptr;              // -k ln(z / k), z = 0 .. k
+  uint32_t cap = 0;
+  bool detect_issued = false;
+  uint32_t last_threshold = 0;
+  // host path (Sec. 4.1): two staging buffers and a copy stream
+  uint32_t* staging[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_free[2] = {nullptr, nullptr};
+
+  uint8_t* seav(uint32_t router) const { return sketches + (uint64_t)router * stride; }
+  uint32_t* ldca(uint32_t router) const { return reinterpret_cast<uint32_t*>(sketches + (uint64_t)router * stride + seav_pad); }
+};
+
+extern "C" {
+
+int sp_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+const char* sp_strerror(int code) {
+  switch (code) {
+    case SP_OK: return "ok";
+    case SP_WARN_THETA_BELOW_INIT: return "warning: detect threshold below the theta that fixed tau";
+    case SP_ERR_PARAM: return "invalid argument or parameter set";
+    case SP_ERR_ROUTER: return "router index out of range";
+    case SP_ERR_TRUNCATED: return "more results than the output capacity";
+    case SP_ERR_CANDIDATE_OVERFLOW: return "candidate buffer or join bound overflowed; results incomplete";
+    case SP_ERR_CUDA: return "CUDA runtime error";
+    case SP_ERR_TIMEOUT: return "bounded wait timed out";
+    case SP_ERR_CHECKSUM: return "sketch image checksum or parameter mismatch";
+    case SP_ERR_NOMEM: return "allocation failed";
+    case SP_ERR_STATE: return "call not valid in the current state";
+    default: return "unknown status";
+  }
+}
+
+int sp_default_params(sp_params* out) {
+  if (!out) return SP_ERR_PARAM;
+  memset(out, 0, sizeof(*out));
+  out->r = 14;
+  out->sr = 4;
+  const uint32_t L = 32 - out->r, step = (L + out->sr - 1) / out->sr, a = 2;
+  for (uint32_t i = 0; i < out->sr; ++i) {
+    out->isb[i] = i * step;
+    out->ibn[i] = step + a;
+  }
+  out->k_log2 = 10;
+  out->lr = 4;
+  out->lc_log2 = 16;
+  out->theta = 1024;
+  out->n_routers = 1;
+  out->window_slices = 1;
+  out->max_candidates = 0;
+  out->seed = 0x5EED;
+  out->max_join = 0;
+  return SP_OK;
+}
+
+int sp_check_params(const sp_params* p) {
+  if (!p) return SP_ERR_PARAM;
+  if (p->r > 24 || p->sr < 1 || p->sr > 8) return SP_ERR_PARAM;
+  const uint32_t L = 32 - p->r;
+  for (uint32_t i = 0; i < p->sr; ++i) {
+    if (p->ibn[i] < 1 || p->ibn[i] > 12 || p->ibn[i] > L || p->isb[i] >= L) return SP_ERR_PARAM;
+  }
+  if (sea_bytes_of(p) > 4096) return SP_ERR_PARAM;
+  // constraint 1 (Sec. 3.2): every LP bit lies in some row's index
+  for (uint32_t bit = 0; bit < L; ++bit) {
+    bool covered = false;
+    for (uint32_t i = 0; i < p->sr && !covered; ++i) covered = row_covers(p->isb[i], p->ibn[i], L, bit);
+    if (!covered) return SP_ERR_PARAM;
+  }
+  // constraint 2 (Sec. 3.2), read as: row i shares an LP bit with row i + 1 mod SR
+  if (p->sr > 1) {
+    for (uint32_t i = 0; i < p->sr; ++i) {
+      const uint32_t n = (i + 1) % p->sr;
+      bool shared = false;
+      for (uint32_t bit = 0; bit < L && !shared; ++bit)
+        shared = row_covers(p->isb[i], p->ibn[i], L, bit) && row_covers(p->isb[n], p->ibn[n], L, bit);
+      if (!shared) return SP_ERR_PARAM;
+    }
+  }
+  if (p->k_log2 < 5 || p->k_log2 > 16) return SP_ERR_PARAM;
+  if (p->lr < 1 || p->lr > 8 || p->lc_log2 > 24) return SP_ERR_PARAM;
+  if ((uint64_t)p->lr << (p->lc_log2 + p->k_log2) > (1ull << 32)) return SP_ERR_PARAM;
+  if (p->theta == 0) return SP_ERR_PARAM;
+  if (p->n_routers < 1 || p->n_routers > 4096) return SP_ERR_PARAM;
+  if (p->window_slices != 1) return SP_ERR_PARAM;
+  return SP_OK;
+}
+
+int sp_sketch_bytes(const sp_params* p, uint64_t* seav_bytes, uint64_t* ldca_bytes) {
+  if (sp_check_params(p) != SP_OK) return SP_ERR_PARAM;
+  if (seav_bytes) *seav_bytes = sea_bytes_of(p) << p->r;
+  if (ldca_bytes) *ldca_bytes = ((uint64_t)p->lr << (p->lc_log2 + p->k_log2)) / 8;
+  return SP_OK;
+}
+
+uint32_t sp_tau(uint32_t theta) {
+  // Eq. 1: tau = ceil(log2(theta / 8)), at least 0: smallest t with 8 * 2^t >= theta
+  uint32_t t = 0;
+  while (t < 29 && (8ull << t) < (uint64_t)theta) ++t;
+  return t;
+}
+
+static double est_of(uint32_t k_log2, uint32_t z) {
+  const double k = (double)(1ull << k_log2);
+  return -k * log((double)z / k);   // Eq. 4
+}
+
+uint32_t sp_z_theta(uint32_t k_log2, uint32_t threshold) {
+  const uint32_t k = 1u << k_log2;
+  for (uint32_t z = k; z > 0; --z)
+    if (est_of(k_log2, z) >= (double)threshold) return z;
+  return 0;
+}
+
+void sp_destroy(sp_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->copy_stream) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamDestroy(ctx->copy_stream);
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (ctx->ev_copied[i]) cudaEventDestroy(ctx->ev_copied[i]);
+    if (ctx->ev_free[i]) cudaEventDestroy(ctx->ev_free[i]);
+    if (ctx->staging[i]) cudaFree(ctx->staging[i]);
+  }
+  cudaFree(ctx->sketches);
+  cudaFree(ctx->keys);
+  cudaFree(ctx->records);
+  cudaFree(ctx->status);
+  cudaFree(ctx->est_table);
+  delete ctx;
+}
+
+int sp_create(const sp_params* p, void* cuda_stream, sp_ctx** out) {
+  if (!out) return SP_ERR_PARAM;
+  *out = nullptr;
+  if (sp_check_params(p) != SP_OK) return SP_ERR_PARAM;
+  sp_ctx* c = new (std::nothrow) sp_ctx();
+  if (!c) return SP_ERR_NOMEM;
+  c->p = *p;
+  if (c->p.max_candidates == 0) c->p.max_candidates = (uint32_t)kDefaultMaxCandidates;
+  if (c->p.max_join == 0) c->p.max_join = kDefaultMaxJoin;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaGetDevice(&c->device);
+
+  DevParams& d = c->d;
+  memset(&d, 0, sizeof(d));
+  uint64_t s = p->seed;
+  for (uint32_t i = 0; i < 2 + p->lr; ++i) {
+    d.ha[i] = splitmix64_next(&s);
+    d.hb[i] = splitmix64_next(&s);
+  }
+  d.r = p->r;
+  d.L = 32 - p->r;
+  d.sr = p->sr;
+  d.tau = sp_tau(p->theta);
+  d.k_log2 = p->k_log2;
+  d.lr = p->lr;
+  d.lc_log2 = p->lc_log2;
+  uint32_t off = 0;
+  for (uint32_t i = 0; i < p->sr; ++i) {
+    d.isb[i] = p->isb[i];
+    d.ibn[i] = p->ibn[i];
+    d.row_off[i] = off;
+    d.cover[i] = sp::spread_idx((1u << p->ibn[i]) - 1u, p->isb[i], d.L);
+    off += 1u << p->ibn[i];
+  }
+  d.sea_bytes = off;
+  sp_sketch_bytes(p, &c->seav_bytes, &c->ldca_bytes);
+  d.seav_bytes = c->seav_bytes;
+  d.ldca_words = c->ldca_bytes / 4;
+  c->seav_pad = align_up(c->seav_bytes, kAlign);
+  c->stride = c->seav_pad + align_up(c->ldca_bytes, kAlign);
+  c->cap = c->p.max_candidates;
+  const uint64_t key_slots = 1ull << log2_ceil_u64(c->cap);
+
+  int rc = SP_OK;
+  if (cudaMalloc(&c->sketches, c->stride * p->n_routers) != cudaSuccess ||
+      cudaMalloc(&c->keys, key_slots * sizeof(uint64_t)) != cudaSuccess ||
+      cudaMalloc(&c->records, (uint64_t)c->cap * sizeof(sp_candidate)) != cudaSuccess ||
+      cudaMalloc(&c->status, sizeof(DetectStatus)) != cudaSuccess ||
+      cudaMalloc(&c->est_table, ((1ull << p->k_log2) + 1) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    rc = SP_ERR_NOMEM;
+  }
+  if (rc == SP_OK) {
+    const uint32_t k = 1u << p->k_log2;
+    double* table = static_cast<double*>(malloc((k + 1) * sizeof(double)));
+    if (!table) rc = SP_ERR_NOMEM;
+    else {
+      table[0] = (double)k * log((double)k);   // saturated union: reported as k ln k
+      for (uint32_t z = 1; z <= k; ++z) table[z] = est_of(p->k_log2, z);
+      if (cudaMemcpy(c->est_table, table, (k + 1) * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = SP_ERR_CUDA;
+      free(table);
+    }
+  }
+  if (rc == SP_OK && sp::launch_zero(c->sketches, c->stride * p->n_routers, c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
+  if (rc == SP_OK && cudaMemsetAsync(c->status, 0, sizeof(DetectStatus), c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
+  if (rc == SP_OK) c->scan_grid = sp::scan_grid(d);
+  if (rc == SP_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
+  if (rc != SP_OK) {
+    sp_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return SP_OK;
+}
+
+int sp_set_stream(sp_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return SP_ERR_PARAM;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  return SP_OK;
+}
+
+int sp_get_params(const sp_ctx* ctx, sp_params* out) {
+  if (!ctx || !out) return SP_ERR_PARAM;
+  *out = ctx->p;
+  return SP_OK;
+}
+
+int sp_reset(sp_ctx* ctx, uint32_t router) {
+  if (!ctx) return SP_ERR_PARAM;
+  if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
+  return sp::launch_zero(ctx->seav(router), ctx->stride, ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+}
+
+int sp_update(sp_ctx* ctx, uint32_t router, const uint32_t* dev_pairs, uint64_t n_pairs) {
+  if (!ctx) return SP_ERR_PARAM;
+  if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
+  if (n_pairs == 0) return SP_OK;
+  if (!dev_pairs || ((uintptr_t)dev_pairs & 7u)) return SP_ERR_PARAM;
+  return sp::launch_scan(ctx->d, ctx->seav(router), ctx->ldca(router), dev_pairs, n_pairs,
+                         ctx->scan_grid, ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+}
+
+static int ensure_staging(sp_ctx* ctx) {
+  if (ctx->staging[0]) return SP_OK;
+  for (int i = 0; i < 2; ++i) {
+    if (cudaMalloc(&ctx->staging[i], kStagingPairs * 8) != cudaSuccess) { cudaGetLastError(); return SP_ERR_NOMEM; }
+    if (cudaEventCreateWithFlags(&ctx->ev_copied[i], cudaEventDisableTiming) != cudaSuccess) return SP_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&ctx->ev_free[i], cudaEventDisableTiming) != cudaSuccess) return SP_ERR_CUDA;
+  }
+  if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) return SP_ERR_CUDA;
+  return SP_OK;
+}
+
+int sp_update_host(sp_ctx* ctx, uint32_t router, const uint32_t* host_pairs, uint64_t n_pairs) {
+  if (!ctx) return SP_ERR_PARAM;
+  if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
+  if (n_pairs == 0) return SP_OK;
+  if (!host_pairs) return SP_ERR_PARAM;
+  int rc = ensure_staging(ctx);
+  if (rc != SP_OK) return rc;
+  // the copy stream must not overtake work already queued on the main stream
+  // that still reads a staging buffer: ev_free[b] marks the last scan of b
+  uint64_t done = 0;
+  uint32_t j = 0;
+  while (done < n_pairs) {
+    const uint32_t b = j & 1u;
+    const uint64_t m = (n_pairs - done) < kStagingPairs ? (n_pairs - done) : kStagingPairs;
+    if (j >= 2 || ctx->ev_free[b]) {
+      if (cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[b], 0) != cudaSuccess) return SP_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(ctx->staging[b], host_pairs + 2 * done, m * 8, cudaMemcpyHostToDevice,
+                        ctx->copy_stream) != cudaSuccess) return SP_ERR_CUDA;
+    if (cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream) != cudaSuccess) return SP_ERR_CUDA;
+    if (cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[b], 0) != cudaSuccess) return SP_ERR_CUDA;
+    if (sp::launch_scan(ctx->d, ctx->seav(router), ctx->ldca(router), ctx->staging[b], m,
+                        ctx->scan_grid, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+    if (cudaEventRecord(ctx->ev_free[b], ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+    done += m;
+    ++j;
+  }
+  return SP_OK;
+}
+
+int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
+                      const uint32_t* const* dev_pairs, const uint64_t* n_pairs) {
+  if (!ctx) return SP_ERR_PARAM;
+  if (n_batches == 0) return SP_OK;
+  if (!routers || !dev_pairs || !n_pairs) return SP_ERR_PARAM;
+  for (uint32_t b = 0; b < n_batches; ++b) {
+    if (routers[b] >= ctx->p.n_routers) return SP_ERR_ROUTER;
+    if (n_pairs[b] && (!dev_pairs[b] || ((uintptr_t)dev_pairs[b] & 7u))) return SP_ERR_PARAM;
+  }
+  for (uint32_t b = 0; b < n_batches; ++b) {
+    int rc = sp_update(ctx, routers[b], dev_pairs[b], n_pairs[b]);
+    if (rc != SP_OK) return rc;
+  }
+  return SP_OK;
+}
+
+int sp_merge(sp_ctx* ctx, const uint32_t* routers, uint32_t n, uint32_t dst_router) {
+  if (!ctx || (n && !routers)) return SP_ERR_PARAM;
+  if (dst_router >= ctx->p.n_routers) return SP_ERR_ROUTER;
+  const uint8_t* srcs[4096];
+  uint32_t m = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (routers[i] >= ctx->p.n_routers) return SP_ERR_ROUTER;
+    if (routers[i] == dst_router) continue;   // x | x = x
+    if (m < 4096) srcs[m++] = ctx->seav(routers[i]);
+  }
+  return sp::launch_merge(ctx->seav(dst_router), srcs, m, ctx->stride, ctx->stream) == cudaSuccess
+             ? SP_OK : SP_ERR_CUDA;
+}
+
+int sp_detect_async(sp_ctx* ctx, uint32_t router, uint32_t threshold) {
+  if (!ctx) return SP_ERR_PARAM;
+  if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
+  if (threshold == 0) threshold = ctx->p.theta;
+  const uint32_t zt = sp_z_theta(ctx->p.k_log2, threshold);
+  if (cudaMemsetAsync(ctx->status, 0, sizeof(DetectStatus), ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+  if (sp::launch_detect(ctx->d, ctx->seav(router), ctx->ldca(router), zt, ctx->keys, ctx->cap,
+                        ctx->p.max_join, ctx->status, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+  if (sp::launch_sort_emit(ctx->keys, ctx->cap, ctx->status, ctx->est_table, ctx->p.k_log2,
+                           ctx->records, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+  ctx->detect_issued = true;
+  ctx->last_threshold = threshold;
+  return threshold < ctx->p.theta ? SP_WARN_THETA_BELOW_INIT : SP_OK;
+}
+
+int sp_results(sp_ctx* ctx, sp_candidate* host_out, uint64_t cap, uint64_t* n_total) {
+  if (!ctx || !n_total || (cap && !host_out)) return SP_ERR_PARAM;
+  if (!ctx->detect_issued) return SP_ERR_STATE;
+  DetectStatus st;
+  if (cudaMemcpyAsync(&st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+  *n_total = st.count;
+  const uint64_t avail = st.count < ctx->cap ? st.count : ctx->cap;
+  const uint64_t m = avail < cap ? avail : cap;
+  if (m) {
+    if (cudaMemcpyAsync(host_out, ctx->records, m * sizeof(sp_candidate), cudaMemcpyDeviceToHost,
+                        ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+  }
+  if (st.overflow) return SP_ERR_CANDIDATE_OVERFLOW;
+  if (st.count > cap) return SP_ERR_TRUNCATED;
+  return SP_OK;
+}
+
+int sp_detect(sp_ctx* ctx, uint32_t router, uint32_t threshold,
+              sp_candidate* host_out, uint64_t cap, uint64_t* n_total) {
+  int w = sp_detect_async(ctx, router, threshold);
+  if (w < 0) return w;
+  int rc = sp_results(ctx, host_out, cap, n_total);
+  return rc != SP_OK ? rc : w;
+}
+
+int sp_results_device(sp_ctx* ctx, const sp_candidate** dev_records, const uint32_t** dev_count) {
+  if (!ctx || !dev_records || !dev_count) return SP_ERR_PARAM;
+  *dev_records = ctx->records;
+  *dev_count = &ctx->status->count;
+  return SP_OK;
+}
+
+int sp_slide(sp_ctx* ctx, uint32_t router) {
+  if (!ctx) return SP_ERR_PARAM;
+  return sp_reset(ctx, router);
+}
+
+int sp_export(sp_ctx* ctx, uint32_t router, void* host_buf, uint64_t cap, uint64_t* n) {
+  if (!ctx || !n) return SP_ERR_PARAM;
+  if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
+  const uint64_t total = sizeof(ImageHeader) + ctx->seav_bytes + ctx->ldca_bytes + 8;
+  *n = total;
+  if (!host_buf) return SP_OK;
+  if (cap < total) return SP_ERR_TRUNCATED;
+  ImageHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, "SPSKETCH", 8);
+  h.version = 1;
+  h.header_bytes = sizeof(ImageHeader);
+  h.r = ctx->p.r; h.sr = ctx->p.sr;
+  memcpy(h.isb, ctx->p.isb, sizeof(h.isb));
+  memcpy(h.ibn, ctx->p.ibn, sizeof(h.ibn));
+  h.k_log2 = ctx->p.k_log2; h.lr = ctx->p.lr; h.lc_log2 = ctx->p.lc_log2; h.theta = ctx->p.theta;
+  h.seed = ctx->p.seed;
+  h.seav_bytes = ctx->seav_bytes;
+  h.ldca_bytes = ctx->ldca_bytes;
+  uint8_t* out = static_cast<uint8_t*>(host_buf);
+  memcpy(out, &h, sizeof(h));
+  if (cudaMemcpyAsync(out + sizeof(h), ctx->seav(router), ctx->seav_bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+      cudaMemcpyAsync(out + sizeof(h) + ctx->seav_bytes, ctx->ldca(router), ctx->ldca_bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+  const uint64_t sum = fnv1a64(out, total - 8);
+  memcpy(out + total - 8, &sum, 8);
+  return SP_OK;
+}
+
+int sp_import(sp_ctx* ctx, uint32_t router, const void* host_buf, uint64_t n) {
+  if (!ctx || !host_buf) return SP_ERR_PARAM;
+  if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
+  const uint64_t total = sizeof(ImageHeader) + ctx->seav_bytes + ctx->ldca_bytes + 8;
+  if (n != total) return SP_ERR_CHECKSUM;
+  const uint8_t* in = static_cast<const uint8_t*>(host_buf);
+  uint64_t sum;
+  memcpy(&sum, in + total - 8, 8);
+  if (fnv1a64(in, total - 8) != sum) return SP_ERR_CHECKSUM;
+  ImageHeader h;
+  memcpy(&h, in, sizeof(h));
+  if (memcmp(h.magic, "SPSKETCH", 8) != 0 || h.version != 1 || h.header_bytes != sizeof(ImageHeader) ||
+      h.r != ctx->p.r || h.sr != ctx->p.sr || memcmp(h.isb, ctx->p.isb, sizeof(h.isb)) != 0 ||
+      memcmp(h.ibn, ctx->p.ibn, sizeof(h.ibn)) != 0 || h.k_log2 != ctx->p.k_log2 || h.lr != ctx->p.lr ||
+      h.lc_log2 != ctx->p.lc_log2 || h.theta != ctx->p.theta || h.seed != ctx->p.seed ||
+      h.seav_bytes != ctx->seav_bytes || h.ldca_bytes != ctx->ldca_bytes)
+    return SP_ERR_CHECKSUM;
+  if (cudaMemcpyAsync(ctx->seav(router), in + sizeof(h), ctx->seav_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+      cudaMemcpyAsync(ctx->ldca(router), in + sizeof(h) + ctx->seav_bytes, ctx->ldca_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+  return SP_OK;
+}
+
+}  // extern "C"

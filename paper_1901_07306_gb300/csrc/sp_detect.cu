@@ -1,0 +1,250 @@
+// sp_detect.cu -- end-of-window restore and filter (Sec. 3.2-3.3, Sec. 4.2).
+//
+// k_detect: one warp per SEA (grid-stride over the 2^r SEAs).
+//   1. HSE(i): lanes test 32 SEs of a row at a time for weight >= 3 and a
+//      ballot/popc prefix compacts the hot columns into a per-warp list in
+//      shared memory (Sec. 3.2, "hot SE").
+//   2. CIS: lanes split the product HSE(0) x HSE(1); each lane then walks
+//      rows 2 .. SR-1 depth first.  A partial tuple is dropped as soon as two
+//      rows disagree on a shared LP bit (it then matches no LP) or the AND of
+//      its SEs falls below weight 3 -- AND only clears bits, so the pruning
+//      loses nothing against testing complete tuples (Sec. 3.2, SEU test).
+//   3. A complete tuple fixes every LP bit (Eq. 3, coverage constraint);
+//      ip = LP << r | RP.  Its LDC union (AND over the LR rows, Sec. 3.3) is
+//      read as LR lines of k bits; z0 = k - popc.  The host survives when
+//      z0 <= Z_theta, the integer form of Est >= threshold (Eq. 4).
+//   Survivors are appended as (ip << 32 | z0) keys with one atomic per hit.
+// k_sort_emit: one block sorts the keys (bitonic, in shared memory when they
+//   fit, else in global memory) and writes sp_candidate records with
+//   est taken from a per-context table of -k ln(z0 / k).
+#include "sp_internal.h"
+
+namespace sp {
+
+namespace {
+
+constexpr int kDetectWarps = 8;
+constexpr int kDetectThreads = kDetectWarps * 32;
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+struct Found {
+  uint64_t* keys;
+  uint32_t cap;
+  uint64_t max_join;
+  DetectStatus* status;
+};
+
+__device__ __forceinline__ uint32_t ldc_zeros(const DevParams& d, const uint32_t* __restrict__ ldca, uint32_t ip) {
+  const uint32_t wpl = 1u << (d.k_log2 - 5u);
+  const uint32_t cshift = 32u - d.lc_log2;
+  const uint32_t* line[8];
+  for (uint32_t i = 0; i < d.lr; ++i) {
+    const uint32_t col = (uint32_t)((uint64_t)mas(d.ha[2 + i], d.hb[2 + i], ip) >> cshift);
+    line[i] = ldca + ((uint64_t)((i << d.lc_log2) | col) << (d.k_log2 - 5u));
+  }
+  uint32_t ones = 0;
+  if (wpl >= 4) {
+    for (uint32_t w = 0; w < wpl; w += 4) {
+      uint4 u = *reinterpret_cast<const uint4*>(line[0] + w);
+      for (uint32_t i = 1; i < d.lr; ++i) {
+        const uint4 v = *reinterpret_cast<const uint4*>(line[i] + w);
+        u.x &= v.x; u.y &= v.y; u.z &= v.z; u.w &= v.w;
+      }
+      ones += __popc(u.x) + __popc(u.y) + __popc(u.z) + __popc(u.w);
+    }
+  } else {
+    for (uint32_t w = 0; w < wpl; ++w) {
+      uint32_t u = line[0][w];
+      for (uint32_t i = 1; i < d.lr; ++i) u &= line[i][w];
+      ones += __popc(u);
+    }
+  }
+  return (1u << d.k_log2) - ones;
+}
+
+// One complete, consistent tuple: reconstruct the IP and apply the filter.
+// Returns false when the detect must stop (a bound was hit).
+__device__ __forceinline__ bool emit_lp(const DevParams& d, const uint32_t* __restrict__ ldca,
+                                        uint32_t rp, uint32_t lp, uint32_t z_theta,
+                                        const Found& f, uint32_t& join_local) {
+  if (++join_local == 64u) {
+    const unsigned long long prev = atomicAdd(reinterpret_cast<unsigned long long*>(&f.status->join), 64ull);
+    join_local = 0;
+    if (prev + 64ull > f.max_join) { atomicOr(&f.status->overflow, 2u); return false; }
+  }
+  const uint32_t ip = (uint32_t)(((uint64_t)lp << d.r) | rp);
+  const uint32_t z0 = ldc_zeros(d, ldca, ip);
+  if (z0 <= z_theta) {
+    const uint32_t slot = atomicAdd(&f.status->count, 1u);
+    if (slot < f.cap) f.keys[slot] = ((uint64_t)ip << 32) | z0;
+    else atomicOr(&f.status->overflow, 1u);
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kDetectThreads)
+k_detect(DevParams d, const uint8_t* __restrict__ seav, const uint32_t* __restrict__ ldca,
+         uint32_t z_theta, Found f) {
+  extern __shared__ uint16_t s_lists[];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  uint16_t* lists = s_lists + warp * d.sea_bytes;       // row i list at lists + row_off[i]
+  const uint32_t n_sea = 1u << d.r;
+  uint32_t join_local = 0;
+  bool stop = false;
+  for (uint32_t rp = blockIdx.x * kDetectWarps + warp; rp < n_sea && !stop; rp += gridDim.x * kDetectWarps) {
+    // warp-uniform: lane 0 reads the flag, every lane sees its value
+    uint32_t ov = lane == 0 ? *reinterpret_cast<volatile uint32_t*>(&f.status->overflow) : 0u;
+    ov = __shfl_sync(kFull, ov, 0);
+    if (ov & 2u) break;
+    const uint8_t* sea = seav + (uint64_t)rp * d.sea_bytes;
+    // 1. hot SEs per row
+    uint32_t cnt[8];
+    bool empty = false;
+    for (uint32_t i = 0; i < d.sr; ++i) {
+      const uint32_t sc = 1u << d.ibn[i];
+      uint32_t n = 0;
+      for (uint32_t c0 = 0; c0 < sc; c0 += 32) {
+        const uint32_t c = c0 + lane;
+        const bool hot = c < sc && __popc((uint32_t)sea[d.row_off[i] + c]) >= 3;
+        const uint32_t bal = __ballot_sync(kFull, hot);
+        if (hot) lists[d.row_off[i] + n + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)c;
+        n += __popc(bal);
+      }
+      cnt[i] = n;
+      empty |= (n == 0);
+    }
+    __syncwarp();
+    if (!empty) {
+      // 2. lanes split HSE(0) x HSE(1); depth-first over the remaining rows
+      const uint32_t n1 = d.sr > 1 ? cnt[1] : 1u;
+      const uint32_t total = cnt[0] * n1;
+      for (uint32_t t = lane; t < total && !stop; t += 32) {
+        const uint32_t c0 = lists[d.row_off[0] + t / n1];
+        uint32_t km = d.cover[0];
+        uint32_t kv = spread_idx(c0, d.isb[0], d.L);
+        uint32_t seu = sea[d.row_off[0] + c0];
+        uint32_t start = 1;
+        if (d.sr > 1) {
+          const uint32_t c1 = lists[d.row_off[1] + t % n1];
+          const uint32_t v1 = spread_idx(c1, d.isb[1], d.L);
+          if (((v1 ^ kv) & d.cover[1] & km) != 0u) continue;
+          seu &= sea[d.row_off[1] + c1];
+          if (__popc(seu) < 3) continue;
+          km |= d.cover[1];
+          kv |= v1;
+          start = 2;
+        }
+        if (start == d.sr) {
+          if (!emit_lp(d, ldca, rp, kv, z_theta, f, join_local)) stop = true;
+          continue;
+        }
+        uint32_t pos[8], skm[8], skv[8], sseu[8];
+        int dd = (int)start;
+        pos[dd] = 0; skm[dd] = km; skv[dd] = kv; sseu[dd] = seu;
+        while (dd >= (int)start && !stop) {
+          if (pos[dd] >= cnt[dd]) {
+            if (--dd >= (int)start) ++pos[dd];
+            continue;
+          }
+          const uint32_t c = lists[d.row_off[dd] + pos[dd]];
+          const uint32_t v = spread_idx(c, d.isb[dd], d.L);
+          const uint32_t s2 = sseu[dd] & sea[d.row_off[dd] + c];
+          if (((v ^ skv[dd]) & d.cover[dd] & skm[dd]) == 0u && __popc(s2) >= 3) {
+            if (dd == (int)d.sr - 1) {
+              if (!emit_lp(d, ldca, rp, skv[dd] | v, z_theta, f, join_local)) stop = true;
+              ++pos[dd];
+            } else {
+              const int nx = dd + 1;
+              pos[nx] = 0; skm[nx] = skm[dd] | d.cover[dd]; skv[nx] = skv[dd] | v; sseu[nx] = s2;
+              dd = nx;
+            }
+          } else {
+            ++pos[dd];
+          }
+        }
+      }
+    }
+    __syncwarp();
+    stop = __any_sync(kFull, stop);
+  }
+  if (join_local) atomicAdd(reinterpret_cast<unsigned long long*>(&f.status->join), (unsigned long long)join_local);
+}
+
+// ---- sort + emit ----------------------------------------------------------
+constexpr int kSortThreads = 1024;
+constexpr uint32_t kSmemSortCap = 8192;   // 64 KiB of keys
+
+__device__ __forceinline__ void emit_record(uint64_t key, const double* est_table, sp_candidate* out) {
+  sp_candidate c;
+  c.ip = (uint32_t)(key >> 32);
+  c.z0 = (uint32_t)key;
+  c.est = est_table[c.z0];
+  c.flags = c.z0 == 0u ? SP_FLAG_SATURATED : 0u;
+  c.pad = 0u;
+  *out = c;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_emit(uint64_t* keys, uint32_t cap, const DetectStatus* status, const double* est_table,
+            sp_candidate* out) {
+  extern __shared__ uint64_t s_keys[];
+  const uint32_t n = min(status->count, cap);
+  if (n == 0) return;
+  uint32_t m = 1;
+  while (m < n) m <<= 1;
+  const bool in_smem = m <= kSmemSortCap;
+  uint64_t* a = in_smem ? s_keys : keys;   // global buffer holds a power of two >= cap
+  for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+    if (in_smem) a[i] = i < n ? keys[i] : ~0ull;
+    else if (i >= n) a[i] = ~0ull;
+  }
+  __syncthreads();
+  // bitonic sort, ascending
+  for (uint32_t size = 2; size <= m; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t i = threadIdx.x; i < m / 2; i += blockDim.x) {
+        const uint32_t lo = 2 * i - (i & (stride - 1));
+        const uint32_t hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const uint64_t x = a[lo], y = a[hi];
+        if ((x > y) == up) { a[lo] = y; a[hi] = x; }
+      }
+      if (!in_smem) __threadfence_block();
+      __syncthreads();
+    }
+  }
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) emit_record(a[i], est_table, out + i);
+}
+
+}  // namespace
+
+cudaError_t launch_detect(const DevParams& d, const uint8_t* seav, const uint32_t* ldca,
+                          uint32_t z_theta, uint64_t* keys, uint32_t cap, uint64_t max_join,
+                          DetectStatus* status, cudaStream_t s) {
+  const size_t smem = (size_t)kDetectWarps * d.sea_bytes * sizeof(uint16_t);
+  cudaError_t e = cudaFuncSetAttribute(k_detect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_detect, kDetectThreads, smem);
+  if (per_sm < 1) per_sm = 1;
+  const uint64_t n_sea = 1ull << d.r;
+  uint64_t grid = (n_sea + kDetectWarps - 1) / kDetectWarps;
+  if (grid > (uint64_t)sms * per_sm) grid = (uint64_t)sms * per_sm;
+  Found f{keys, cap, max_join, status};
+  k_detect<<<(unsigned)grid, kDetectThreads, smem, s>>>(d, seav, ldca, z_theta, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort_emit(uint64_t* keys, uint32_t cap, const DetectStatus* status,
+                             const double* est_table, uint32_t /*k_log2*/,
+                             sp_candidate* out, cudaStream_t s) {
+  const size_t smem = kSmemSortCap * sizeof(uint64_t);
+  cudaError_t e = cudaFuncSetAttribute(k_sort_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_sort_emit<<<1, kSortThreads, smem, s>>>(keys, cap, status, est_table, out);
+  return cudaGetLastError();
+}
+
+}  // namespace sp

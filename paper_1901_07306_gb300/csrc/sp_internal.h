@@ -1,0 +1,74 @@
+// sp_internal.h -- device-side parameter block and kernel launchers of the
+// super point library (arXiv 1901.07306, Sec. 3-5).  Private to csrc/.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/superpoint.h"
+
+namespace sp {
+
+// Everything a kernel needs, derived once from sp_params at sp_create.
+struct DevParams {
+  uint64_t ha[10];          // multiply-add-shift words: 0 = H1, 1 = H3, 2 + i = LH_i
+  uint64_t hb[10];
+  uint32_t r;               // RP bits (Sec. 3.2)
+  uint32_t L;               // LP bits = 32 - r
+  uint32_t sr;              // SEA rows
+  uint32_t tau;             // Eq. 1
+  uint32_t k_log2;          // LDC bits (Sec. 3.3)
+  uint32_t lr;              // LDCA rows
+  uint32_t lc_log2;         // LDCA columns
+  uint32_t sea_bytes;       // bytes of one SEA = sum SC(i)
+  uint32_t isb[8];          // Def. 3
+  uint32_t ibn[8];          // Def. 4
+  uint32_t row_off[8];      // byte offset of row i inside an SEA
+  uint32_t cover[8];        // LP bits covered by row i (Eq. 2), as a mask
+  uint64_t seav_bytes;      // 2^r * sea_bytes
+  uint64_t ldca_words;      // lr * LC * k / 32
+};
+
+// Detect status word, one per context, device resident.
+struct DetectStatus {
+  uint32_t count;           // super points found (may exceed the buffer)
+  uint32_t overflow;        // bit 0: result buffer full, bit 1: join bound hit
+  uint64_t join;            // LPs that reached the LDCA test
+};
+
+// Multiply-add-shift hash (Dietzfelbinger 1996): top 32 bits of
+// (a * x + b) mod 2^64, written as one wide and one narrow multiply-add.
+__host__ __device__ __forceinline__ uint32_t mas(uint64_t a, uint64_t b, uint32_t x) {
+  const uint64_t lo = (uint64_t)(uint32_t)a * x + b;
+  return (uint32_t)(lo >> 32) + (uint32_t)(a >> 32) * x;
+}
+
+// Places index bits of row i at their LP positions (inverse of Eq. 2,
+// i.e. Eq. 3): index bit j goes to LP bit (isb + j) mod L.
+__host__ __device__ __forceinline__ uint32_t spread_idx(uint32_t c, uint32_t isb, uint32_t L) {
+  const uint64_t t = (uint64_t)c << isb;
+  const uint64_t maskL = (L == 32) ? 0xFFFFFFFFull : ((1ull << L) - 1);
+  return (uint32_t)((t | (t >> L)) & maskL);
+}
+
+// Eq. 2: Idx(i, LP) = bits isb .. isb + ibn - 1 of LP, cyclically mod L.
+__host__ __device__ __forceinline__ uint32_t gather_idx(uint32_t lp, uint32_t isb, uint32_t ibn, uint32_t L) {
+  const uint64_t twice = (uint64_t)lp | ((uint64_t)lp << L);
+  return (uint32_t)(twice >> isb) & ((1u << ibn) - 1u);
+}
+
+// ---- launchers (return cudaGetLastError() of the launch) -------------------
+cudaError_t launch_zero(void* dev, uint64_t bytes, cudaStream_t s);
+cudaError_t launch_scan(const DevParams& d, uint8_t* seav, uint32_t* ldca,
+                        const uint32_t* pairs, uint64_t n_pairs, int grid, cudaStream_t s);
+int scan_grid(const DevParams& d);
+cudaError_t launch_merge(uint8_t* dst, const uint8_t* const* srcs, uint32_t n_src,
+                         uint64_t bytes, cudaStream_t s);
+cudaError_t launch_detect(const DevParams& d, const uint8_t* seav, const uint32_t* ldca,
+                          uint32_t z_theta, uint64_t* keys, uint32_t cap, uint64_t max_join,
+                          DetectStatus* status, cudaStream_t s);
+cudaError_t launch_sort_emit(uint64_t* keys, uint32_t cap, const DetectStatus* status,
+                             const double* est_table, uint32_t k_log2,
+                             sp_candidate* out, cudaStream_t s);
+
+}  // namespace sp

@@ -1,0 +1,100 @@
+"""Host-side checks of the C ABI library: it builds, loads, exports every
+entry point include/superpoint.h declares, and its host logic (parameter
+validation, Eq. 1, the integer form of Eq. 4, sizes) agrees with the
+paper's closed forms.  No GPU compute is issued here."""
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sp():
+    from paper_1901_07306_gb300 import build
+    build.build()
+    from paper_1901_07306_gb300 import sp as mod
+    return mod
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "superpoint.h")).read()
+    return sorted(set(re.findall(r"^SP_API [\w\s\*]+?\b(sp_\w+)\(", text, flags=re.M)))
+
+
+def test_exports_every_declared_symbol(sp):
+    names = _declared()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(sp.lib, name), name
+    assert set(names) == set(sp.EXPORTED)
+
+
+def test_header_cites_the_paper():
+    text = open(os.path.join(ROOT, "include", "superpoint.h")).read()
+    for ref in ["Sec. 3.1", "Sec. 3.2", "Sec. 3.3", "Sec. 4.1", "Sec. 4.2", "Sec. 5", "Eq. 1", "Eq. 2",
+                "Eq. 3", "Eq. 4"]:
+        assert ref in text, ref
+
+
+def test_version_and_strerror(sp):
+    assert sp.lib.sp_version() >= 10000
+    assert sp.lib.sp_strerror(sp.SP_ERR_CANDIDATE_OVERFLOW).decode().startswith("candidate")
+    assert sp.lib.sp_strerror(12345).decode() == "unknown status"
+
+
+def test_default_profile(sp):
+    p = sp.sp_default_params()
+    assert (p.r, p.sr, list(p.isb[:4]), list(p.ibn[:4])) == (14, 4, [0, 5, 10, 15], [7, 7, 7, 7])
+    assert (p.k_log2, p.lr, p.lc_log2, p.theta, p.n_routers, p.window_slices) == (10, 4, 16, 1024, 1, 1)
+    assert sp.sp_sketch_bytes(p) == (8 << 20, 32 << 20)
+    assert sp.sp_check_params(p) == 0
+
+
+def test_tau_and_z_theta(sp):
+    for theta in list(range(1, 3000)) + [2**31, 2**32 - 1]:
+        assert sp.sp_tau(theta) == max(0, (theta - 1).bit_length() - 3)
+    assert sp.sp_z_theta(10, 1024) == 376
+    for k_log2 in (5, 8, 10, 12, 16):
+        k = 1 << k_log2
+        for thr in (1, 7, 100, 1024, 4000, 10**5):
+            b = k * math.exp(-thr / k)
+            if abs(b - round(b)) > 1e-9:
+                assert sp.sp_z_theta(k_log2, thr) == math.floor(b)
+
+
+def test_param_validation_matches_oracle(sp):
+    import oracle as O
+    cases = [
+        dict(),
+        dict(r=12, isb=(0, 7, 14), ibn=(8, 8, 8), k_log2=8, lr=3, lc_log2=6),
+        dict(isb=(0, 5, 10), ibn=(7, 7, 7)),            # LP bit 17 uncovered
+        dict(isb=(0, 7, 10, 15)),                      # rows 0, 1 share nothing
+        dict(r=0, isb=(0, 8, 16, 24), ibn=(9, 9, 9, 9)),
+        dict(r=0, isb=(0, 8, 16, 24), ibn=(8, 8, 8, 8)),  # covered, no overlap
+        dict(r=24, isb=(0, 4), ibn=(5, 5)),
+        dict(r=25, isb=(0,), ibn=(7,)),
+        dict(isb=(0,), ibn=(12,), r=20),               # SR = 1 covering all 12 LP bits
+        dict(k_log2=4), dict(k_log2=17), dict(lr=0, ), dict(lr=9), dict(theta=0),
+        dict(ibn=(13, 7, 7, 7)),
+    ]
+    for kw in cases:
+        o = O.Params(**{k: v for k, v in kw.items()})
+        if o.lr < 1 or o.lr > 8:
+            want_ok = False
+        else:
+            want_ok = O.check_params(o) == 0
+        p = sp.make_params(**kw)
+        assert (sp.sp_check_params(p) == 0) == want_ok, kw
+
+
+def test_library_limits(sp):
+    # SEA of more than 4096 bytes is a library limit, not a paper constraint
+    p = sp.make_params(r=8, isb=(0, 12), ibn=(12, 12))
+    assert sp.sp_check_params(p) == sp.SP_ERR_PARAM
+    p = sp.make_params(lr=8, lc_log2=24, k_log2=10)    # 2^37 bits > 2^32
+    assert sp.sp_check_params(p) == sp.SP_ERR_PARAM
+    p = sp.make_params(n_routers=0)
+    assert sp.sp_check_params(p) == sp.SP_ERR_PARAM

@@ -1,0 +1,258 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Sketches (SEAV bytes, LDCA words) and detection lists (ip, z0, est, flags,
+in order) must be bit-identical: the scheme is integer-only up to the
+estimate, and the estimate comes from the same libm on both sides.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1901_07306_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TINY = dict(r=12, isb=(0, 7, 14), ibn=(8, 8, 8), k_log2=8, lr=3, lc_log2=6)
+
+
+@pytest.fixture(scope="module")
+def sp():
+    from paper_1901_07306_gb300 import build
+    build.build()
+    from paper_1901_07306_gb300 import sp as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+def dev(torch, pairs, offset_pairs=0):
+    """Pairs on the GPU as int32; offset_pairs > 0 shifts the start by whole
+    pairs (8 bytes) to exercise the unaligned-head path."""
+    flat = np.ascontiguousarray(pairs, np.uint32).reshape(-1).view(np.int32)
+    buf = torch.empty(flat.size + 2 * offset_pairs + 4, dtype=torch.int32, device="cuda")
+    buf[2 * offset_pairs:2 * offset_pairs + flat.size].copy_(torch.from_numpy(flat))
+    return buf[2 * offset_pairs:2 * offset_pairs + flat.size]
+
+
+def oracle_params(kw):
+    keys = ("r", "isb", "ibn", "k_log2", "lr", "lc_log2", "theta", "seed")
+    return O.Params(**{k: v for k, v in kw.items() if k in keys})
+
+
+def assert_same_sketch(ctx, osk, router=0):
+    seav, ldca = ctx.sketch_image(router)
+    assert seav.shape == osk.seav.shape and ldca.shape == osk.ldca.shape
+    bad = np.nonzero(seav != osk.seav)[0]
+    assert bad.size == 0, f"SEAV differs at {bad[:8]}"
+    bad = np.nonzero(ldca != osk.ldca)[0]
+    assert bad.size == 0, f"LDCA differs at {bad[:8]}"
+
+
+def assert_same_results(got, want):
+    assert len(got) == len(want)
+    for f in ("ip", "z0", "flags"):
+        assert np.array_equal(got[f], want[f]), f
+    assert np.array_equal(got["est"].view(np.uint64), want["est"].view(np.uint64))
+
+
+@pytest.mark.parametrize("n,offset", [(0, 0), (1, 0), (1, 1), (2, 1), (3, 0), (1001, 0), (1001, 1),
+                                       (65537, 0), (200003, 1)])
+def test_scan_parity_sizes_and_alignment(sp, torch, n, offset):
+    kw = dict(TINY, theta=16, seed=7)
+    pairs = W.uniform_pairs(n, seed=n + 3, n_hosts=max(1, n // 20))
+    with sp.SuperPoint(**kw) as ctx:
+        ctx.update(dev(torch, pairs, offset))
+        torch.cuda.synchronize()
+        assert_same_sketch(ctx, O.Sketch(oracle_params(kw)).update(pairs))
+
+
+# (profile, workload) pairs sized so that no SEA is overloaded: the oracle
+# enumerates the full cartesian product of hot SEs, as the paper states it
+PROFILES = [
+    (dict(), dict(n=1 << 17, n_background=4096, n_planted=8, planted_degree=600), 64),      # profile D
+    (dict(r=0, isb=(0, 8, 16, 24), ibn=(9, 9, 9, 9), lc_log2=12),                          # L = 32
+     dict(n=1 << 14, n_background=64, n_planted=4, planted_degree=3000), 1024),
+    (dict(r=16, isb=(0, 8), ibn=(9, 9), lr=1, lc_log2=0, k_log2=5),                        # SR = 2, LC = 1, k = 32
+     dict(n=1 << 17, n_background=4096, n_planted=8, planted_degree=600), 64),
+    (dict(r=16, isb=(0, 3, 6, 9, 12), ibn=(4, 4, 4, 4, 5), lr=8, lc_log2=10, k_log2=12),
+     dict(n=1 << 17, n_background=4096, n_planted=8, planted_degree=600), 64),
+    (dict(r=10, isb=(0, 11), ibn=(12, 12), lr=2, lc_log2=14, k_log2=16),
+     dict(n=1 << 17, n_background=4096, n_planted=8, planted_degree=600), 9),
+]
+
+
+@pytest.mark.parametrize("kw,wl,theta", PROFILES)
+def test_scan_and_detect_parity_profiles(sp, torch, kw, wl, theta):
+    kw = dict(kw, theta=theta, seed=1234)
+    pairs, planted = W.single_window(seed=5, **wl)
+    with sp.SuperPoint(**kw) as ctx:
+        ctx.update(dev(torch, pairs))
+        got, n, rc = ctx.detect()
+        osk = O.Sketch(oracle_params(kw)).update(pairs)
+        assert_same_sketch(ctx, osk)
+        want, n_want, over = osk.detect()
+        assert rc == sp.SP_OK and not over
+        assert n == n_want
+        assert_same_results(got, want)
+        assert set(planted.tolist()) <= set(got["ip"].tolist())
+
+
+def test_single_window_full_size(sp, torch):
+    """2^20 pairs, 20 planted hosts x 3,000 peers, theta 1024, profile D."""
+    pairs, planted = W.single_window(seed=1)
+    kw = dict(seed=1)
+    with sp.SuperPoint(**kw) as ctx:
+        ctx.update(dev(torch, pairs))
+        got, n, rc = ctx.detect(threshold=1024)
+        osk = O.Sketch(oracle_params(kw)).update(pairs)
+        assert_same_sketch(ctx, osk)
+        want, _, _ = osk.detect(1024)
+        assert rc == sp.SP_OK
+        assert_same_results(got, want)
+        assert set(planted.tolist()) <= set(got["ip"].tolist())
+
+
+def test_threshold_sweep_and_warning(sp, torch):
+    pairs, _ = W.single_window(seed=9, n=1 << 18, n_background=16384, n_planted=12,
+                               planted_degree=2500)
+    kw = dict(seed=9)
+    with sp.SuperPoint(**kw) as ctx:
+        ctx.update(dev(torch, pairs))
+        osk = O.Sketch(oracle_params(kw)).update(pairs)
+        for thr in (1024, 1500, 2000, 3000, 6000, 600):
+            got, n, rc = ctx.detect(threshold=thr)
+            want, n2, _ = osk.detect(thr)
+            assert n == n2
+            assert_same_results(got, want)
+            assert rc == (sp.SP_WARN_THETA_BELOW_INIT if thr < 1024 else sp.SP_OK)
+
+
+def test_chunked_updates_and_reset(sp, torch):
+    pairs = W.uniform_pairs(300000, seed=41, n_hosts=2000)
+    kw = dict(TINY, theta=32, seed=41)
+    with sp.SuperPoint(**kw) as ctx:
+        for part in np.array_split(pairs, 7):
+            ctx.update(dev(torch, part))
+        assert_same_sketch(ctx, O.Sketch(oracle_params(kw)).update(pairs))
+        ctx.reset()
+        torch.cuda.synchronize()
+        seav, ldca = ctx.sketch_image()
+        assert not seav.any() and not ldca.any()
+
+
+def test_merge_parity(sp, torch):
+    """Sec. 4.2: OR of the routers' sketches = sketch of the union stream."""
+    routers, sp_hosts = W.distributed(seed=3, n_routers=4, n_per_router=1 << 16, n_global_sp=6,
+                                      sp_range=(1200, 2000), theta=1024)
+    kw = dict(theta=256, seed=77, n_routers=5)
+    with sp.SuperPoint(**kw) as ctx:
+        for i, r in enumerate(routers):
+            ctx.update(dev(torch, r), router=i)
+        ctx.merge([0, 1, 2, 3], 4)
+        op = oracle_params(kw)
+        whole = O.Sketch(op).update(np.concatenate(routers))
+        assert_same_sketch(ctx, whole, router=4)
+        for i, r in enumerate(routers):
+            assert_same_sketch(ctx, O.Sketch(op).update(r), router=i)
+        got, n, rc = ctx.detect(router=4, threshold=1024)
+        want, _, _ = whole.detect(1024)
+        assert_same_results(got, want)
+        # merging into a router listed among the sources is idempotent
+        ctx.merge([4, 0], 4)
+        assert_same_sketch(ctx, whole, router=4)
+
+
+def test_update_host_double_buffer(sp, torch):
+    pairs = W.uniform_pairs((1 << 22) + 12345, seed=8, n_hosts=100000)   # > one staging buffer
+    kw = dict(theta=1024, seed=8)
+    host = torch.from_numpy(pairs.reshape(-1).view(np.int32)).pin_memory()
+    with sp.SuperPoint(**kw) as ctx:
+        ctx.update_host(host)
+        torch.cuda.synchronize()
+        assert_same_sketch(ctx, O.Sketch(oracle_params(kw)).update(pairs))
+        # pageable memory works too
+        ctx.reset()
+        ctx.update_host(pairs)
+        torch.cuda.synchronize()
+        assert_same_sketch(ctx, O.Sketch(oracle_params(kw)).update(pairs))
+
+
+def test_export_import_roundtrip_and_checksum(sp, torch):
+    pairs = W.uniform_pairs(100000, seed=2, n_hosts=500)
+    kw = dict(TINY, theta=16, seed=2, n_routers=2)
+    with sp.SuperPoint(**kw) as ctx:
+        ctx.update(dev(torch, pairs[:60000]))
+        img = sp.sp_export(ctx.ctx, 0)
+        assert sp.sp_import(ctx.ctx, 1, img) == sp.SP_OK
+        ctx.update(dev(torch, pairs[60000:]), router=1)    # resume after checkpoint
+        assert_same_sketch(ctx, O.Sketch(oracle_params(kw)).update(pairs), router=1)
+        bad = bytearray(img)
+        bad[len(bad) // 2] ^= 0x10
+        assert sp.sp_import(ctx.ctx, 0, bytes(bad)) == sp.SP_ERR_CHECKSUM
+        assert sp.sp_import(ctx.ctx, 0, img[:-1]) == sp.SP_ERR_CHECKSUM
+    with sp.SuperPoint(**dict(kw, seed=3)) as other:   # other hash seed: rejected
+        assert sp.sp_import(other.ctx, 0, img) == sp.SP_ERR_CHECKSUM
+
+
+def test_candidate_overflow_and_truncation(sp, torch):
+    pairs, planted = W.single_window(seed=4, n=1 << 18, n_background=8192, n_planted=16,
+                                     planted_degree=2000)
+    kw = dict(seed=4, max_candidates=5)
+    with sp.SuperPoint(**kw) as ctx:
+        ctx.update(dev(torch, pairs))
+        got, n, rc = ctx.detect()
+        assert rc == sp.SP_ERR_CANDIDATE_OVERFLOW and n >= 16 and len(got) == 5
+        want, n_want, _ = O.Sketch(oracle_params(kw)).update(pairs).detect()
+        assert n == n_want
+        assert set(got["ip"].tolist()) <= set(want["ip"].tolist())
+    with sp.SuperPoint(**dict(kw, max_candidates=0)) as ctx:
+        ctx.update(dev(torch, pairs))
+        got, n, rc = sp.sp_detect(ctx.ctx, 0, 0, cap=3)
+        assert rc == sp.SP_ERR_TRUNCATED and len(got) == 3
+        assert_same_results(got, want[:3])
+
+
+def test_join_bound(sp, torch):
+    """A saturated SEAV makes the candidate product explode; the join bound
+    stops the detect with SP_ERR_CANDIDATE_OVERFLOW instead of running on."""
+    pairs = W.uniform_pairs(1 << 20, seed=6, n_hosts=1 << 16)
+    kw = dict(r=4, isb=(0, 7, 14, 21), ibn=(8, 8, 8, 8), theta=1, seed=6, max_join=1 << 12)
+    with sp.SuperPoint(**kw) as ctx:
+        ctx.update(dev(torch, pairs))
+        got, n, rc = ctx.detect(threshold=1)
+        assert rc == sp.SP_ERR_CANDIDATE_OVERFLOW
+
+
+def test_errors(sp, torch):
+    with sp.SuperPoint(**TINY) as ctx:
+        with pytest.raises(sp.SPError) as e:
+            sp.sp_update(ctx.ctx, 3, dev(torch, np.zeros((4, 2), np.uint32)))
+        assert e.value.code == sp.SP_ERR_ROUTER
+        t = torch.zeros(9, dtype=torch.int32, device="cuda")
+        assert sp.lib.sp_update(ctx.ctx, 0, t.data_ptr() + 4, 2) == sp.SP_ERR_PARAM
+        assert sp.lib.sp_results(ctx.ctx, None, 0, sp.ctypes.byref(sp.ctypes.c_uint64())) == sp.SP_ERR_STATE
+    with pytest.raises(sp.SPError):
+        sp.SuperPoint(**dict(TINY, theta=0))
+
+
+def test_core_link_full_size(sp, torch):
+    """The 2^26-pair core-link workload in the launch configuration the
+    benchmark times (one persistent scan launch, one detect), bit-exact
+    against the oracle over the whole sketch and result list."""
+    pairs, planted = W.core_link(seed=2)
+    kw = dict(seed=2)
+    with sp.SuperPoint(**kw) as ctx:
+        ctx.update(dev(torch, pairs))
+        got, n, rc = ctx.detect(threshold=1024)
+        osk = O.Sketch(oracle_params(kw)).update(pairs)
+        assert_same_sketch(ctx, osk)
+        want, _, _ = osk.detect(1024)
+        assert rc == sp.SP_OK
+        assert_same_results(got, want)
+        recall = len(set(planted.tolist()) & set(got["ip"].tolist())) / len(planted)
+        assert recall > 0.95
