@@ -184,12 +184,12 @@ def run_ours(args):
 
     theta = 1024
     seed = args.seed + rank                      # every rank its own watch point
-    pairs, planted = W.core_link(seed=seed)
+    pairs, planted = W.core_link(seed=seed, n=1 << args.pairs_log2)
     n = int(pairs.shape[0])
     flat = torch.from_numpy(pairs.reshape(-1).view(np.int32))
     dev_pairs = flat.cuda()
     stream = torch.cuda.current_stream()
-    params = sp.make_params(seed=seed, theta=theta)
+    params = sp.make_params(seed=seed, theta=theta, scan_mode=args.scan_mode)
     ctx = sp.SuperPoint(params, stream=stream)
     c = ctx.ctx
 
@@ -287,7 +287,8 @@ def run_ours(args):
         "steps": K, "warmup": max(3, args.warmup), "ms_per_step": total_ms / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_pairs": n, "threshold": theta, "profile": "D",
+        "config": {"workload": WORKLOAD if args.pairs_log2 == 26 else f"{WORKLOAD} [scaled to 2^{args.pairs_log2} pairs]",
+                   "n_pairs": n, "threshold": theta, "profile": "D", "scan_mode": args.scan_mode,
                    "l2": "inputs larger than L2 (512 MiB of pairs per step vs 129 MB L2)",
                    "parallelism": f"{world} independent watch point(s), one per GPU"},
         "roofline": {"kernel": "k_scan", "bound": "hbm", "achieved": achieved, "peak": peak,
@@ -321,6 +322,8 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-budget", type=float, default=60.0)
+    ap.add_argument("--pairs-log2", type=int, default=26, help="window size (profiling captures use less)")
+    ap.add_argument("--scan-mode", type=int, default=0, help="0 auto, 1 direct (L2 RED), 2 binned")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -57,6 +57,11 @@ extern "C" {
 #define SP_ERR_NOMEM (-8)            /* device or host allocation failed */
 #define SP_ERR_STATE (-9)            /* call not valid in the context's current state */
 
+/* sp_params.scan_mode */
+#define SP_SCAN_AUTO 0u
+#define SP_SCAN_DIRECT 1u
+#define SP_SCAN_BINNED 2u
+
 /* sp_candidate.flags */
 #define SP_FLAG_SATURATED 1u         /* z0 == 0: the LDC union is full; est = k ln k */
 
@@ -78,10 +83,20 @@ extern "C" {
  * scan time; theta >= 1.
  *
  * n_routers sketches (one per simulated watch point) are held by the context.
- * window_slices = 1 is the discrete window of Sec. 3; > 1 selects the sliding
- * window of Sec. 5 over that many time slices (see sp_slide).
+ * window_slices = 1 is the discrete window of Sec. 3; 2 .. 128 selects the
+ * sliding window W(t, k) of Sec. 5 over k = window_slices time slices: every
+ * SEAV/LDCA bit becomes a one-byte slice stamp (8x the sketch memory), a bit
+ * is active in W(t, k) iff it was set in one of the slices t-k+1 .. t, and
+ * sp_slide() advances t (see there).
  * max_candidates bounds the detect result buffer (0 = 1 << 20).
  * max_join bounds the LPs that reach the LDCA test in one detect (0 = 1 << 26).
+ * scan_mode selects how the LDCA bits of a scan reach memory (results are
+ * identical): SP_SCAN_AUTO (0) picks the binned form for updates of at least
+ * 2^22 pairs when it applies (k <= 4096, LC >= 32, lr * LC <= 2^20), else the
+ * direct form; SP_SCAN_DIRECT (1) sets every bit with an L2 atomic OR;
+ * SP_SCAN_BINNED (2) sorts the pairs by LDC bit position, sets the bits of
+ * each bit plane with shared-memory atomics and folds the planes into the
+ * LDCA before the next detect, merge or export (when it applies).
  * seed seeds the hash family: multiply-add-shift hashes whose (a, b) words are
  * consecutive SplitMix64 outputs for H1, H3, LH_0 .. LH_{lr-1}.
  */
@@ -97,7 +112,7 @@ typedef struct sp_params {
   uint32_t n_routers;
   uint32_t window_slices;
   uint32_t max_candidates;
-  uint32_t reserved0;
+  uint32_t scan_mode;
   uint64_t seed;
   uint64_t max_join;
 } sp_params;
@@ -181,7 +196,10 @@ SP_API int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* ro
 /* Global SEAV/LDCA of Sec. 4.2: dst |= src for every source router, bitwise
  * OR over both structures (the OR of the WPs' sketches equals the sketch of
  * the union of their streams).  routers is a host array of n indices; it may
- * contain dst_router.  Async.  Errors: SP_ERR_ROUTER, SP_ERR_PARAM. */
+ * contain dst_router.  In a sliding context every listed router must be at
+ * the same slice as dst (else SP_ERR_STATE) and each stamp becomes the
+ * youngest of the routers' stamps, which ORs every window.  Async.
+ * Errors: SP_ERR_ROUTER, SP_ERR_PARAM, SP_ERR_STATE. */
 SP_API int sp_merge(sp_ctx* ctx, const uint32_t* routers, uint32_t n, uint32_t dst_router);
 
 /* Restore + filter (Sec. 3.2-3.3) on one router's sketch, enqueued on the
@@ -197,7 +215,8 @@ SP_API int sp_merge(sp_ctx* ctx, const uint32_t* routers, uint32_t n, uint32_t d
 SP_API int sp_detect_async(sp_ctx* ctx, uint32_t router, uint32_t threshold);
 
 /* Waits for the stream, then copies the last detect's results:
- * *n_total = number of super points found; min(*n_total, cap) records go to
+ * *n_total = number of super points found; the first
+ * min(*n_total, max_candidates, cap) records, in ascending ip order, go to
  * host_out (may be NULL when cap = 0).  Errors: SP_ERR_TRUNCATED when
  * *n_total > cap; SP_ERR_CANDIDATE_OVERFLOW when the device result buffer
  * (max_candidates) or the join bound (max_join) overflowed, in which case the
@@ -214,23 +233,29 @@ SP_API int sp_detect(sp_ctx* ctx, uint32_t router, uint32_t threshold,
  * max_candidates on overflow).  No synchronisation. */
 SP_API int sp_results_device(sp_ctx* ctx, const sp_candidate** dev_records, const uint32_t** dev_count);
 
-/* Sliding window (Sec. 5): closes the current time slice of a sliding
- * context and opens the next; bits last set more than window_slices - 1
- * slices ago become inactive ("0") for detect.  Async.  In a discrete
- * context (window_slices = 1) it equals sp_reset.  Errors: SP_ERR_ROUTER. */
+/* Sliding window (Sec. 5): closes the current time slice t of one router of a
+ * sliding context and opens slice t + 1 (t starts at 0 after sp_create or
+ * sp_reset); bits last set more than window_slices - 1 slices ago become
+ * inactive ("0") for detect, merge and export.  Each call also sweeps one of
+ * 255 - window_slices segments of the router's stamps (the per-slice counter
+ * maintenance of Sec. 5.2), so a call costs 1/(255 - k) of a pass over them.
+ * Async.  In a discrete context (window_slices = 1) it equals sp_reset.
+ * Errors: SP_ERR_ROUTER. */
 SP_API int sp_slide(sp_ctx* ctx, uint32_t router);
 
 /* Checkpoint / WP->GS shipment (Sec. 4.2): a self-describing image of one
  * router's sketch in the logical layout -- header, SEAV bytes
  * [2^r][sum SC(i)], LDCA words [lr][LC][k / 32] (bit b of an LDC is bit
  * b % 32 of word b / 32) -- followed by a 64-bit checksum.  With host_buf NULL
- * *n receives the image size.  Synchronises the stream.
+ * *n receives the image size.  A sliding context exports the bits of its
+ * current window.  Synchronises the stream.
  * Errors: SP_ERR_TRUNCATED (cap too small), SP_ERR_ROUTER, SP_ERR_CUDA. */
 SP_API int sp_export(sp_ctx* ctx, uint32_t router, void* host_buf, uint64_t cap, uint64_t* n);
 
 /* Loads an image written by sp_export into a router, replacing its sketch.
  * Rejects an image with a bad checksum or parameters other than the
- * context's (SP_ERR_CHECKSUM) without touching the router. */
+ * context's (SP_ERR_CHECKSUM) without touching the router.  A sliding context
+ * cannot import window bits (SP_ERR_STATE). */
 SP_API int sp_import(sp_ctx* ctx, uint32_t router, const void* host_buf, uint64_t n);
 
 /* Human-readable name of a status code (static storage). */

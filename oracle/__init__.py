@@ -269,3 +269,16 @@ def exact_super_points(pairs: np.ndarray, theta: int) -> np.ndarray:
     """Def. 2: the hosts h with |OP(h)| >= theta, ascending."""
     hosts, counts = exact_opposite_counts(pairs)
     return hosts[counts >= theta]
+
+
+def window_pairs(slices, t: int, k: int) -> np.ndarray:
+    """Sec. 5.1: the sliding window W(t, k) holds the k successive slices
+    ending at slice t (fewer at the start of the stream)."""
+    part = [np.asarray(s, np.uint32).reshape(-1, 2) for s in slices[max(0, t - k + 1):t + 1]]
+    return np.concatenate(part) if part else np.empty((0, 2), np.uint32)
+
+
+def sliding_window_sketch(params: Params, slices, t: int, k: int) -> Sketch:
+    """The sketch a sliding counter pool must expose at slice t (Sec. 5.2:
+    an active counter reads as bit 1): the discrete sketch of W(t, k)."""
+    return Sketch(params).update(window_pairs(slices, t, k))

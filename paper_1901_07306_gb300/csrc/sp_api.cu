@@ -20,6 +20,8 @@ namespace {
 constexpr uint64_t kDefaultMaxCandidates = 1ull << 20;
 constexpr uint64_t kDefaultMaxJoin = 1ull << 26;
 constexpr uint64_t kStagingPairs = 1ull << 22;      // 32 MiB per staging buffer
+constexpr uint64_t kBinnedMinPairs = 1ull << 22;    // auto mode: smaller updates go direct
+constexpr uint64_t kBinnedRoundPairs = 1ull << 26;  // pairs per binning round
 constexpr uint64_t kAlign = 256;
 
 uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
@@ -91,6 +93,19 @@ struct sp_ctx {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_free[2] = {nullptr, nullptr};
+  // binned scan: shared lists, one plane-major accumulator per router
+  sp::BinnedScratch bs;
+  uint32_t** planes = nullptr;              // [n_routers], lazily allocated
+  bool* planes_dirty = nullptr;             // bits not yet folded into the LDCA
+  // sliding window (Sec. 5): one stamp byte per bit, per-router slice clock
+  bool sliding = false;
+  uint8_t* stamps = nullptr;                // n_routers * st_stride bytes
+  uint64_t st_seav_pad = 0, st_stride = 0;
+  uint64_t* slice = nullptr;                // current slice t of each router
+
+  uint8_t* st_seav(uint32_t router) const { return stamps + (uint64_t)router * st_stride; }
+  uint8_t* st_ldca(uint32_t router) const { return stamps + (uint64_t)router * st_stride + st_seav_pad; }
+  uint32_t slice_id(uint32_t router) const { return (uint32_t)(slice[router] % 255u) + 1u; }
 
   uint8_t* seav(uint32_t router) const { return sketches + (uint64_t)router * stride; }
   uint32_t* ldca(uint32_t router) const { return reinterpret_cast<uint32_t*>(sketches + (uint64_t)router * stride + seav_pad); }
@@ -168,7 +183,8 @@ int sp_check_params(const sp_params* p) {
   if ((uint64_t)p->lr << (p->lc_log2 + p->k_log2) > (1ull << 32)) return SP_ERR_PARAM;
   if (p->theta == 0) return SP_ERR_PARAM;
   if (p->n_routers < 1 || p->n_routers > 4096) return SP_ERR_PARAM;
-  if (p->window_slices != 1) return SP_ERR_PARAM;
+  if (p->window_slices < 1 || p->window_slices > 128) return SP_ERR_PARAM;
+  if (p->scan_mode > SP_SCAN_BINNED) return SP_ERR_PARAM;
   return SP_OK;
 }
 
@@ -211,6 +227,15 @@ void sp_destroy(sp_ctx* ctx) {
     if (ctx->ev_free[i]) cudaEventDestroy(ctx->ev_free[i]);
     if (ctx->staging[i]) cudaFree(ctx->staging[i]);
   }
+  if (ctx->planes) {
+    for (uint32_t r = 0; r < ctx->p.n_routers; ++r) cudaFree(ctx->planes[r]);
+    free(ctx->planes);
+  }
+  free(ctx->planes_dirty);
+  free(ctx->slice);
+  cudaFree(ctx->stamps);
+  cudaFree(ctx->bs.lists);
+  cudaFree(ctx->bs.counts);
   cudaFree(ctx->sketches);
   cudaFree(ctx->keys);
   cudaFree(ctx->records);
@@ -285,7 +310,20 @@ int sp_create(const sp_params* p, void* cuda_stream, sp_ctx** out) {
   }
   if (rc == SP_OK && sp::launch_zero(c->sketches, c->stride * p->n_routers, c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
   if (rc == SP_OK && cudaMemsetAsync(c->status, 0, sizeof(DetectStatus), c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
-  if (rc == SP_OK) c->scan_grid = sp::scan_grid(d);
+  if (rc == SP_OK) {
+    c->scan_grid = sp::scan_grid(d);
+    c->planes = static_cast<uint32_t**>(calloc(p->n_routers, sizeof(uint32_t*)));
+    c->planes_dirty = static_cast<bool*>(calloc(p->n_routers, sizeof(bool)));
+    c->slice = static_cast<uint64_t*>(calloc(p->n_routers, sizeof(uint64_t)));
+    if (!c->planes || !c->planes_dirty || !c->slice) rc = SP_ERR_NOMEM;
+  }
+  if (rc == SP_OK && p->window_slices > 1) {
+    c->sliding = true;
+    c->st_seav_pad = align_up(c->seav_bytes * 8, kAlign);
+    c->st_stride = c->st_seav_pad + align_up(c->ldca_bytes * 8, kAlign);
+    if (cudaMalloc(&c->stamps, c->st_stride * p->n_routers) != cudaSuccess) { cudaGetLastError(); rc = SP_ERR_NOMEM; }
+    else if (sp::launch_zero(c->stamps, c->st_stride * p->n_routers, c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
+  }
   if (rc == SP_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
   if (rc != SP_OK) {
     sp_destroy(c);
@@ -307,9 +345,78 @@ int sp_get_params(const sp_ctx* ctx, sp_params* out) {
   return SP_OK;
 }
 
+// Folds a router's pending binned-scan planes into its LDCA.
+static int fold_router(sp_ctx* ctx, uint32_t router) {
+  if (!ctx->planes_dirty[router]) return SP_OK;
+  if (sp::launch_fold(ctx->d, ctx->planes[router], ctx->ldca(router), ctx->bs.fold_grid, ctx->stream) != cudaSuccess)
+    return SP_ERR_CUDA;
+  ctx->planes_dirty[router] = false;
+  return SP_OK;
+}
+
+static int ensure_binned(sp_ctx* ctx, uint32_t router) {
+  if (!ctx->bs.lists) {
+    ctx->bs.ctas = (uint32_t)sp::binned_ctas();
+    ctx->bs.max_pairs = kBinnedRoundPairs;
+    ctx->bs.fold_grid = sp::binned_fold_grid();
+    const uint32_t bins = 1u << ctx->p.k_log2;
+    const uint64_t cap = sp::binned_list_cap(ctx->bs.max_pairs, bins, ctx->bs.ctas);
+    if (cudaMalloc(&ctx->bs.lists, (uint64_t)bins * ctx->bs.ctas * cap * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&ctx->bs.counts, (uint64_t)bins * ctx->bs.ctas * sizeof(uint32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(ctx->bs.lists);
+      ctx->bs.lists = nullptr;
+      return SP_ERR_NOMEM;
+    }
+  }
+  if (!ctx->planes[router]) {
+    if (cudaMalloc(&ctx->planes[router], ctx->ldca_bytes) != cudaSuccess) { cudaGetLastError(); return SP_ERR_NOMEM; }
+    ctx->planes_dirty[router] = false;
+  }
+  return SP_OK;
+}
+
+// One update of one router through the direct or the binned scan.
+static int do_update(sp_ctx* ctx, uint32_t router, const uint32_t* dev_pairs, uint64_t n_pairs) {
+  if (ctx->sliding)
+    return sp::launch_scan_stamp(ctx->d, ctx->st_seav(router), ctx->st_ldca(router), dev_pairs, n_pairs,
+                                 ctx->slice_id(router), ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+  bool binned = false;
+  if (sp::binned_applicable(ctx->d)) {
+    if (ctx->p.scan_mode == SP_SCAN_BINNED) binned = true;
+    else if (ctx->p.scan_mode == SP_SCAN_AUTO) binned = n_pairs >= kBinnedMinPairs;
+  }
+  if (binned) {
+    int rc = ensure_binned(ctx, router);
+    if (rc != SP_OK) return rc;
+    sp::BinnedScratch s = ctx->bs;
+    s.planes = ctx->planes[router];
+    s.accumulate = ctx->planes_dirty[router];
+    if (sp::launch_scan_binned(ctx->d, ctx->seav(router), ctx->ldca(router), dev_pairs, n_pairs, s,
+                               ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+    ctx->planes_dirty[router] = true;
+    return SP_OK;
+  }
+  return sp::launch_scan(ctx->d, ctx->seav(router), ctx->ldca(router), dev_pairs, n_pairs,
+                         ctx->scan_grid, ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+}
+
+// Sliding contexts: the current window's bits into the router's SEAV/LDCA.
+static int materialize(sp_ctx* ctx, uint32_t router) {
+  if (!ctx->sliding) return SP_OK;
+  return sp::launch_materialize(ctx->st_seav(router), ctx->seav(router), ctx->seav_bytes, ctx->st_ldca(router),
+                                ctx->ldca(router), ctx->ldca_bytes / 4, ctx->slice_id(router),
+                                ctx->p.window_slices, ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+}
+
 int sp_reset(sp_ctx* ctx, uint32_t router) {
   if (!ctx) return SP_ERR_PARAM;
   if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
+  ctx->planes_dirty[router] = false;     // pending planes belong to the old window
+  if (ctx->sliding) {
+    ctx->slice[router] = 0;
+    if (sp::launch_zero(ctx->st_seav(router), ctx->st_stride, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+  }
   return sp::launch_zero(ctx->seav(router), ctx->stride, ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
 }
 
@@ -318,8 +425,7 @@ int sp_update(sp_ctx* ctx, uint32_t router, const uint32_t* dev_pairs, uint64_t 
   if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
   if (n_pairs == 0) return SP_OK;
   if (!dev_pairs || ((uintptr_t)dev_pairs & 7u)) return SP_ERR_PARAM;
-  return sp::launch_scan(ctx->d, ctx->seav(router), ctx->ldca(router), dev_pairs, n_pairs,
-                         ctx->scan_grid, ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+  return do_update(ctx, router, dev_pairs, n_pairs);
 }
 
 static int ensure_staging(sp_ctx* ctx) {
@@ -354,8 +460,8 @@ int sp_update_host(sp_ctx* ctx, uint32_t router, const uint32_t* host_pairs, uin
                         ctx->copy_stream) != cudaSuccess) return SP_ERR_CUDA;
     if (cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream) != cudaSuccess) return SP_ERR_CUDA;
     if (cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[b], 0) != cudaSuccess) return SP_ERR_CUDA;
-    if (sp::launch_scan(ctx->d, ctx->seav(router), ctx->ldca(router), ctx->staging[b], m,
-                        ctx->scan_grid, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+    rc = do_update(ctx, router, ctx->staging[b], m);
+    if (rc != SP_OK) return rc;
     if (cudaEventRecord(ctx->ev_free[b], ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
     done += m;
     ++j;
@@ -384,8 +490,23 @@ int sp_merge(sp_ctx* ctx, const uint32_t* routers, uint32_t n, uint32_t dst_rout
   if (dst_router >= ctx->p.n_routers) return SP_ERR_ROUTER;
   const uint8_t* srcs[4096];
   uint32_t m = 0;
-  for (uint32_t i = 0; i < n; ++i) {
+  for (uint32_t i = 0; i < n; ++i)
     if (routers[i] >= ctx->p.n_routers) return SP_ERR_ROUTER;
+  if (ctx->sliding) {
+    const uint8_t* ssrc[4096];
+    uint32_t ms = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+      if (ctx->slice[routers[i]] != ctx->slice[dst_router]) return SP_ERR_STATE;   // one slice clock
+      if (routers[i] != dst_router && ms < 4096) ssrc[ms++] = ctx->st_seav(routers[i]);
+    }
+    return sp::launch_merge_stamp(ctx->st_seav(dst_router), ssrc, ms, ctx->st_stride, ctx->slice_id(dst_router),
+                                  ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+  }
+  int rc = fold_router(ctx, dst_router);
+  if (rc != SP_OK) return rc;
+  for (uint32_t i = 0; i < n; ++i) {
+    rc = fold_router(ctx, routers[i]);
+    if (rc != SP_OK) return rc;
     if (routers[i] == dst_router) continue;   // x | x = x
     if (m < 4096) srcs[m++] = ctx->seav(routers[i]);
   }
@@ -398,6 +519,9 @@ int sp_detect_async(sp_ctx* ctx, uint32_t router, uint32_t threshold) {
   if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
   if (threshold == 0) threshold = ctx->p.theta;
   const uint32_t zt = sp_z_theta(ctx->p.k_log2, threshold);
+  int frc = fold_router(ctx, router);
+  if (frc == SP_OK) frc = materialize(ctx, router);
+  if (frc != SP_OK) return frc;
   if (cudaMemsetAsync(ctx->status, 0, sizeof(DetectStatus), ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
   if (sp::launch_detect(ctx->d, ctx->seav(router), ctx->ldca(router), zt, ctx->keys, ctx->cap,
                         ctx->p.max_join, ctx->status, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
@@ -444,7 +568,16 @@ int sp_results_device(sp_ctx* ctx, const sp_candidate** dev_records, const uint3
 
 int sp_slide(sp_ctx* ctx, uint32_t router) {
   if (!ctx) return SP_ERR_PARAM;
-  return sp_reset(ctx, router);
+  if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
+  if (!ctx->sliding) return sp_reset(ctx, router);   // discrete window: the next period starts empty
+  ctx->slice[router] += 1;
+  // sweep segment (t mod M) of the router's counters, M = 255 - k
+  const uint64_t M = 255u - ctx->p.window_slices;
+  const uint64_t units = ctx->st_stride / 16;
+  const uint64_t seg = ctx->slice[router] % M;
+  const uint64_t lo = units * seg / M * 16, hi = units * (seg + 1) / M * 16;
+  return sp::launch_clean(ctx->st_seav(router) + lo, 0, hi - lo, ctx->slice_id(router), ctx->p.window_slices,
+                          ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
 }
 
 int sp_export(sp_ctx* ctx, uint32_t router, void* host_buf, uint64_t cap, uint64_t* n) {
@@ -454,6 +587,9 @@ int sp_export(sp_ctx* ctx, uint32_t router, void* host_buf, uint64_t cap, uint64
   *n = total;
   if (!host_buf) return SP_OK;
   if (cap < total) return SP_ERR_TRUNCATED;
+  int frc = fold_router(ctx, router);
+  if (frc == SP_OK) frc = materialize(ctx, router);
+  if (frc != SP_OK) return frc;
   ImageHeader h;
   memset(&h, 0, sizeof(h));
   memcpy(h.magic, "SPSKETCH", 8);
@@ -479,6 +615,7 @@ int sp_export(sp_ctx* ctx, uint32_t router, void* host_buf, uint64_t cap, uint64
 int sp_import(sp_ctx* ctx, uint32_t router, const void* host_buf, uint64_t n) {
   if (!ctx || !host_buf) return SP_ERR_PARAM;
   if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
+  if (ctx->sliding) return SP_ERR_STATE;   // an image holds window bits, not slice stamps
   const uint64_t total = sizeof(ImageHeader) + ctx->seav_bytes + ctx->ldca_bytes + 8;
   if (n != total) return SP_ERR_CHECKSUM;
   const uint8_t* in = static_cast<const uint8_t*>(host_buf);
@@ -493,6 +630,7 @@ int sp_import(sp_ctx* ctx, uint32_t router, const void* host_buf, uint64_t n) {
       h.lc_log2 != ctx->p.lc_log2 || h.theta != ctx->p.theta || h.seed != ctx->p.seed ||
       h.seav_bytes != ctx->seav_bytes || h.ldca_bytes != ctx->ldca_bytes)
     return SP_ERR_CHECKSUM;
+  ctx->planes_dirty[router] = false;
   if (cudaMemcpyAsync(ctx->seav(router), in + sizeof(h), ctx->seav_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
       cudaMemcpyAsync(ctx->ldca(router), in + sizeof(h) + ctx->seav_bytes, ctx->ldca_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;

@@ -57,11 +57,39 @@ __host__ __device__ __forceinline__ uint32_t gather_idx(uint32_t lp, uint32_t is
   return (uint32_t)(twice >> isb) & ((1u << ibn) - 1u);
 }
 
+// Scratch of the binned scan (sp_scan_binned.cu), shared by a context's routers.
+struct BinnedScratch {
+  uint32_t* lists = nullptr;    // [bins][ctas][cap] hips
+  uint32_t* counts = nullptr;   // [bins][ctas]
+  uint32_t* planes = nullptr;   // [k][LR * LC / 32] plane-major accumulator of one router
+  bool accumulate = false;      // planes hold earlier bits (load instead of zero)
+  uint32_t ctas = 0;            // persistent binning blocks
+  uint64_t max_pairs = 0;       // pairs per binning round the lists are sized for
+  int fold_grid = 0;
+};
+
 // ---- launchers (return cudaGetLastError() of the launch) -------------------
 cudaError_t launch_zero(void* dev, uint64_t bytes, cudaStream_t s);
 cudaError_t launch_scan(const DevParams& d, uint8_t* seav, uint32_t* ldca,
                         const uint32_t* pairs, uint64_t n_pairs, int grid, cudaStream_t s);
 int scan_grid(const DevParams& d);
+bool binned_applicable(const DevParams& d);
+uint32_t binned_list_cap(uint64_t n_pairs, uint32_t bins, uint32_t ctas);
+int binned_ctas();
+int binned_fold_grid();
+// scan with the LDCA bits accumulated in s.planes (no fold)
+cudaError_t launch_scan_binned(const DevParams& d, uint8_t* seav, uint32_t* ldca, const uint32_t* pairs,
+                               uint64_t n_pairs, const BinnedScratch& s, cudaStream_t st);
+// ldca |= transpose(planes)
+cudaError_t launch_fold(const DevParams& d, const uint32_t* planes, uint32_t* ldca, int grid, cudaStream_t st);
+// sliding window (sp_slide.cu)
+cudaError_t launch_scan_stamp(const DevParams& d, uint8_t* st_seav, uint8_t* st_ldca, const uint32_t* pairs,
+                              uint64_t n_pairs, uint32_t id, cudaStream_t s);
+cudaError_t launch_clean(uint8_t* stamps, uint64_t lo, uint64_t hi, uint32_t cur, uint32_t k, cudaStream_t s);
+cudaError_t launch_materialize(const uint8_t* st_seav, uint8_t* seav, uint64_t seav_bytes, const uint8_t* st_ldca,
+                               uint32_t* ldca, uint64_t ldca_words, uint32_t cur, uint32_t k, cudaStream_t s);
+cudaError_t launch_merge_stamp(uint8_t* dst, const uint8_t* const* srcs, uint32_t n_src, uint64_t bytes,
+                               uint32_t cur, cudaStream_t s);
 cudaError_t launch_merge(uint8_t* dst, const uint8_t* const* srcs, uint32_t n_src,
                          uint64_t bytes, cudaStream_t s);
 cudaError_t launch_detect(const DevParams& d, const uint8_t* seav, const uint32_t* ldca,

@@ -31,6 +31,7 @@ SP_ERR_CHECKSUM = -7
 SP_ERR_NOMEM = -8
 SP_ERR_STATE = -9
 SP_FLAG_SATURATED = 1
+SP_SCAN_AUTO, SP_SCAN_DIRECT, SP_SCAN_BINNED = 0, 1, 2
 
 EXPORTED = (
     "sp_version", "sp_strerror", "sp_default_params", "sp_check_params", "sp_sketch_bytes",
@@ -48,7 +49,7 @@ class sp_params(ctypes.Structure):
         ("k_log2", ctypes.c_uint32), ("lr", ctypes.c_uint32), ("lc_log2", ctypes.c_uint32),
         ("theta", ctypes.c_uint32), ("n_routers", ctypes.c_uint32),
         ("window_slices", ctypes.c_uint32), ("max_candidates", ctypes.c_uint32),
-        ("reserved0", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("max_join", ctypes.c_uint64),
+        ("scan_mode", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("max_join", ctypes.c_uint64),
     ]
 
 
@@ -123,14 +124,14 @@ def sp_default_params() -> sp_params:
 
 def make_params(r=14, isb=(0, 5, 10, 15), ibn=(7, 7, 7, 7), k_log2=10, lr=4, lc_log2=16,
                 theta=1024, n_routers=1, window_slices=1, max_candidates=0, seed=0x5EED,
-                max_join=0) -> sp_params:
+                max_join=0, scan_mode=0) -> sp_params:
     p = sp_params()
     p.r, p.sr = r, len(isb)
     for i, (s, b) in enumerate(zip(isb, ibn)):
         p.isb[i], p.ibn[i] = s, b
     p.k_log2, p.lr, p.lc_log2, p.theta = k_log2, lr, lc_log2, theta
     p.n_routers, p.window_slices, p.max_candidates = n_routers, window_slices, max_candidates
-    p.seed, p.max_join = seed & (2**64 - 1), max_join
+    p.seed, p.max_join, p.scan_mode = seed & (2**64 - 1), max_join, scan_mode
     return p
 
 
@@ -190,8 +191,9 @@ def _pairs_ptr(pairs):
         if not pairs.is_contiguous():
             raise ValueError("pairs must be contiguous")
         return pairs.data_ptr(), pairs.numel() // 2
-    arr = np.ascontiguousarray(pairs)
-    return arr.ctypes.data, arr.size // 2
+    if not (isinstance(pairs, np.ndarray) and pairs.flags.c_contiguous and pairs.dtype.itemsize == 4):
+        raise ValueError("host pairs must be a C-contiguous 4-byte integer array (the library borrows it)")
+    return pairs.ctypes.data, pairs.size // 2
 
 
 def sp_update(ctx: int, router: int, dev_pairs) -> None:
@@ -237,7 +239,8 @@ def sp_results(ctx: int, cap: int | None = None):
     out = np.zeros(max(cap, 1), CANDIDATE)
     rc = lib.sp_results(ctypes.c_void_p(ctx), ctypes.c_void_p(out.ctypes.data), cap, ctypes.byref(n))
     _check(rc, "sp_results", ok=(SP_OK, SP_ERR_TRUNCATED, SP_ERR_CANDIDATE_OVERFLOW))
-    return out[:min(cap, n.value)], n.value, rc
+    written = min(cap, n.value, sp_get_params(ctx).max_candidates)
+    return out[:written], n.value, rc
 
 
 def sp_detect(ctx: int, router: int = 0, threshold: int = 0, cap: int | None = None):

@@ -390,3 +390,30 @@ def test_lemma1_psu_monte_carlo():
     # as the error scale: each row's LDC fill varies by ~binomial(N/LC)
     got = ones / (len(probes) * k)
     assert abs(got - psu) < 0.25 * psu
+
+
+# ------------------------------------------------- Sec. 5.1 sliding window --
+def test_sliding_boundary_worked_example():
+    """The Sec. 5.1 example, by exact counts (Def. 1, Def. 2)."""
+    spec = {ln[0]: ln[1:] for ln in _golden_lines("sliding_boundary_example.txt")}
+    theta, k = int(spec["theta"][0]), int(spec["slices_per_window"][0])
+    per = [int(x) for x in spec["peers_per_slice"]]
+    rng = np.random.default_rng(245)
+    aip = 0xC0A80042
+    slices = []
+    for n in per:
+        bg = W.uniform_pairs(3000, seed=int(rng.integers(1 << 30)), n_hosts=500)
+        own = np.stack([np.full(n, aip, np.uint32), rng.integers(0, 2**32, n, dtype=np.uint32)], 1)
+        slices.append(np.concatenate([bg, own]))
+    dw1 = O.window_pairs(slices, k - 1, k)
+    dw2 = O.window_pairs(slices, 2 * k - 1, k)
+    tw = O.window_pairs(slices, k + 1, k)
+    for pairs, want in ((dw1, spec["expect_dw1"]), (dw2, spec["expect_dw2"]), (tw, spec["expect_tw"])):
+        assert (aip in set(O.exact_super_points(pairs, theta).tolist())) == bool(int(want[0]))
+
+
+def test_window_pairs_definition():
+    slices = [np.full((i + 1, 2), i, np.uint32) for i in range(6)]
+    assert O.window_pairs(slices, 0, 3).shape == (1, 2)
+    w = O.window_pairs(slices, 4, 3)
+    assert sorted(set(w[:, 0].tolist())) == [2, 3, 4] and w.shape[0] == 3 + 4 + 5

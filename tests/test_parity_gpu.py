@@ -39,6 +39,15 @@ def dev(torch, pairs, offset_pairs=0):
     return buf[2 * offset_pairs:2 * offset_pairs + flat.size]
 
 
+_CORE = {}
+
+
+def _core_link():
+    if "pairs" not in _CORE:
+        _CORE["pairs"] = W.core_link(seed=2)
+    return _CORE["pairs"]
+
+
 def oracle_params(kw):
     keys = ("r", "isb", "ibn", "k_log2", "lr", "lc_log2", "theta", "seed")
     return O.Params(**{k: v for k, v in kw.items() if k in keys})
@@ -60,10 +69,14 @@ def assert_same_results(got, want):
     assert np.array_equal(got["est"].view(np.uint64), want["est"].view(np.uint64))
 
 
+MODES = [1, 2]   # SP_SCAN_DIRECT, SP_SCAN_BINNED
+
+
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("n,offset", [(0, 0), (1, 0), (1, 1), (2, 1), (3, 0), (1001, 0), (1001, 1),
                                        (65537, 0), (200003, 1)])
-def test_scan_parity_sizes_and_alignment(sp, torch, n, offset):
-    kw = dict(TINY, theta=16, seed=7)
+def test_scan_parity_sizes_and_alignment(sp, torch, n, offset, mode):
+    kw = dict(TINY, theta=16, seed=7, scan_mode=mode)
     pairs = W.uniform_pairs(n, seed=n + 3, n_hosts=max(1, n // 20))
     with sp.SuperPoint(**kw) as ctx:
         ctx.update(dev(torch, pairs, offset))
@@ -81,14 +94,15 @@ PROFILES = [
      dict(n=1 << 17, n_background=4096, n_planted=8, planted_degree=600), 64),
     (dict(r=16, isb=(0, 3, 6, 9, 12), ibn=(4, 4, 4, 4, 5), lr=8, lc_log2=10, k_log2=12),
      dict(n=1 << 17, n_background=4096, n_planted=8, planted_degree=600), 64),
-    (dict(r=10, isb=(0, 11), ibn=(12, 12), lr=2, lc_log2=14, k_log2=16),
+    (dict(r=12, isb=(0, 10), ibn=(11, 11), lr=2, lc_log2=14, k_log2=16),             # 4 KiB SEA (limit), k = 2^16
      dict(n=1 << 17, n_background=4096, n_planted=8, planted_degree=600), 9),
 ]
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("kw,wl,theta", PROFILES)
-def test_scan_and_detect_parity_profiles(sp, torch, kw, wl, theta):
-    kw = dict(kw, theta=theta, seed=1234)
+def test_scan_and_detect_parity_profiles(sp, torch, kw, wl, theta, mode):
+    kw = dict(kw, theta=theta, seed=1234, scan_mode=mode)
     pairs, planted = W.single_window(seed=5, **wl)
     with sp.SuperPoint(**kw) as ctx:
         ctx.update(dev(torch, pairs))
@@ -102,10 +116,11 @@ def test_scan_and_detect_parity_profiles(sp, torch, kw, wl, theta):
         assert set(planted.tolist()) <= set(got["ip"].tolist())
 
 
-def test_single_window_full_size(sp, torch):
+@pytest.mark.parametrize("mode", MODES)
+def test_single_window_full_size(sp, torch, mode):
     """2^20 pairs, 20 planted hosts x 3,000 peers, theta 1024, profile D."""
     pairs, planted = W.single_window(seed=1)
-    kw = dict(seed=1)
+    kw = dict(seed=1, scan_mode=mode)
     with sp.SuperPoint(**kw) as ctx:
         ctx.update(dev(torch, pairs))
         got, n, rc = ctx.detect(threshold=1024)
@@ -132,9 +147,10 @@ def test_threshold_sweep_and_warning(sp, torch):
             assert rc == (sp.SP_WARN_THETA_BELOW_INIT if thr < 1024 else sp.SP_OK)
 
 
-def test_chunked_updates_and_reset(sp, torch):
+@pytest.mark.parametrize("mode", MODES)
+def test_chunked_updates_and_reset(sp, torch, mode):
     pairs = W.uniform_pairs(300000, seed=41, n_hosts=2000)
-    kw = dict(TINY, theta=32, seed=41)
+    kw = dict(TINY, theta=32, seed=41, scan_mode=mode)
     with sp.SuperPoint(**kw) as ctx:
         for part in np.array_split(pairs, 7):
             ctx.update(dev(torch, part))
@@ -145,11 +161,12 @@ def test_chunked_updates_and_reset(sp, torch):
         assert not seav.any() and not ldca.any()
 
 
-def test_merge_parity(sp, torch):
+@pytest.mark.parametrize("mode", MODES)
+def test_merge_parity(sp, torch, mode):
     """Sec. 4.2: OR of the routers' sketches = sketch of the union stream."""
     routers, sp_hosts = W.distributed(seed=3, n_routers=4, n_per_router=1 << 16, n_global_sp=6,
                                       sp_range=(1200, 2000), theta=1024)
-    kw = dict(theta=256, seed=77, n_routers=5)
+    kw = dict(theta=256, seed=77, n_routers=5, scan_mode=mode)
     with sp.SuperPoint(**kw) as ctx:
         for i, r in enumerate(routers):
             ctx.update(dev(torch, r), router=i)
@@ -167,9 +184,10 @@ def test_merge_parity(sp, torch):
         assert_same_sketch(ctx, whole, router=4)
 
 
-def test_update_host_double_buffer(sp, torch):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_update_host_double_buffer(sp, torch, mode):
     pairs = W.uniform_pairs((1 << 22) + 12345, seed=8, n_hosts=100000)   # > one staging buffer
-    kw = dict(theta=1024, seed=8)
+    kw = dict(theta=1024, seed=8, scan_mode=mode)
     host = torch.from_numpy(pairs.reshape(-1).view(np.int32)).pin_memory()
     with sp.SuperPoint(**kw) as ctx:
         ctx.update_host(host)
@@ -182,9 +200,10 @@ def test_update_host_double_buffer(sp, torch):
         assert_same_sketch(ctx, O.Sketch(oracle_params(kw)).update(pairs))
 
 
-def test_export_import_roundtrip_and_checksum(sp, torch):
+@pytest.mark.parametrize("mode", MODES)
+def test_export_import_roundtrip_and_checksum(sp, torch, mode):
     pairs = W.uniform_pairs(100000, seed=2, n_hosts=500)
-    kw = dict(TINY, theta=16, seed=2, n_routers=2)
+    kw = dict(TINY, theta=16, seed=2, n_routers=2, scan_mode=mode)
     with sp.SuperPoint(**kw) as ctx:
         ctx.update(dev(torch, pairs[:60000]))
         img = sp.sp_export(ctx.ctx, 0)
@@ -240,18 +259,61 @@ def test_errors(sp, torch):
         sp.SuperPoint(**dict(TINY, theta=0))
 
 
-def test_core_link_full_size(sp, torch):
+def test_binned_pending_planes(sp, torch):
+    """Several binned updates accumulate in the plane buffer; detect, merge,
+    export and reset see exactly the oracle's sketch at every point."""
+    kw = dict(theta=256, seed=31, n_routers=3, scan_mode=2)
+    op = oracle_params(kw)
+    a = W.uniform_pairs(1 << 18, seed=31, n_hosts=20000)
+    b, _ = W.single_window(seed=32, n=1 << 18, n_background=8192, n_planted=6, planted_degree=900)
+    with sp.SuperPoint(**kw) as ctx:
+        ctx.update(dev(torch, a), router=0)
+        ctx.update(dev(torch, b[:100000]), router=0)          # accumulate on pending planes
+        ctx.update(dev(torch, b[100000:]), router=0)
+        ora = O.Sketch(op).update(a).update(b)
+        got, n, rc = ctx.detect(router=0)
+        want, _, _ = ora.detect()
+        assert_same_results(got, want)
+        assert_same_sketch(ctx, ora, router=0)
+        ctx.update(dev(torch, a), router=1)
+        ctx.update(dev(torch, b), router=2)
+        ctx.merge([1, 2], 0)                                   # sources still pending
+        assert_same_sketch(ctx, ora, router=0)
+        ctx.update(dev(torch, b), router=1)
+        ctx.reset(1)                                           # drops the pending planes
+        ctx.update(dev(torch, a[:5000]), router=1)
+        assert_same_sketch(ctx, O.Sketch(op).update(a[:5000]), router=1)
+
+
+def test_binned_list_overflow_skew(sp, torch):
+    """Every pair has the same opposite IP, so all of them fall into one bit
+    plane: the per-block lists overflow and the rest goes through L2 REDs."""
+    n = 1 << 20
+    rng = np.random.default_rng(12)
+    pairs = np.stack([rng.integers(0, 2**32, n, dtype=np.uint32),
+                      np.full(n, 0x0A000001, np.uint32)], 1)
+    pairs[: n // 2, 1] = rng.integers(0, 2**32, n // 2, dtype=np.uint32)   # half skewed
+    kw = dict(seed=12, scan_mode=2)
+    with sp.SuperPoint(**kw) as ctx:
+        ctx.update(dev(torch, pairs))
+        assert_same_sketch(ctx, O.Sketch(oracle_params(kw)).update(pairs))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_core_link_full_size(sp, torch, mode):
     """The 2^26-pair core-link workload in the launch configuration the
-    benchmark times (one persistent scan launch, one detect), bit-exact
-    against the oracle over the whole sketch and result list."""
-    pairs, planted = W.core_link(seed=2)
-    kw = dict(seed=2)
+    benchmark times (one scan call, one detect), bit-exact against the oracle
+    over the whole sketch and result list."""
+    pairs, planted = _core_link()
+    kw = dict(seed=2, scan_mode=mode)
     with sp.SuperPoint(**kw) as ctx:
         ctx.update(dev(torch, pairs))
         got, n, rc = ctx.detect(threshold=1024)
-        osk = O.Sketch(oracle_params(kw)).update(pairs)
+        if "oracle" not in _CORE:
+            osk = O.Sketch(oracle_params(kw)).update(pairs)
+            _CORE["oracle"] = (osk, osk.detect(1024)[0])
+        osk, want = _CORE["oracle"]
         assert_same_sketch(ctx, osk)
-        want, _, _ = osk.detect(1024)
         assert rc == sp.SP_OK
         assert_same_results(got, want)
         recall = len(set(planted.tolist()) & set(got["ip"].tolist())) / len(planted)
