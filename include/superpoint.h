@@ -258,6 +258,43 @@ SP_API int sp_export(sp_ctx* ctx, uint32_t router, void* host_buf, uint64_t cap,
  * cannot import window bits (SP_ERR_STATE). */
 SP_API int sp_import(sp_ctx* ctx, uint32_t router, const void* host_buf, uint64_t n);
 
+/* Limits of sp_detect_noalloc. */
+#define SP_NOALLOC_MAX_RESULTS 65536u
+#define SP_NOALLOC_MAX_K_LOG2 12u
+
+/* Detect without allocating.  The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory when they detect --
+ * code recorded into a CUDA stream capture, programs whose device memory is
+ * owned or budgeted by another allocator, and latency-critical loops that
+ * cannot take an allocation (or its failure) on their path.  It runs the same
+ * restore and filter as sp_detect_async on a sketch the caller holds:
+ *   p          parameters the sketch was built with (validated; discrete
+ *              window only; k_log2 <= SP_NOALLOC_MAX_K_LOG2)
+ *   dev_seav   one router's SEAV, device memory, the sp_export layout
+ *   dev_ldca   its LDCA, device memory, 16-byte aligned, the sp_export layout
+ *   threshold  0 means p->theta
+ *   dev_out    device array of cap records, sorted by ascending ip
+ *              (min(count, cap) are written); may be NULL when cap = 0
+ *   cap        at most SP_NOALLOC_MAX_RESULTS
+ *   dev_status two device uint32 words: [0] = super points found (may exceed
+ *              cap; then the list holds an unspecified subset), [1] = overflow
+ *              flags (1: more than cap found, 2: the join bound was hit)
+ *   cuda_stream the stream the work is enqueued on (async)
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch
+ * is one fixed array of about 556 KiB in the library's device image, held by
+ * every GPU that loads the library until the process exits.  The first call
+ * on each device looks up that array's device address (cudaGetSymbolAddress
+ * with the device current); make that first call before any stream capture.
+ * All calls on a device share the array and it keeps the last call's contents
+ * (each call resets what must start from zero): calls that overlap on the GPU
+ * -- on different streams, or from different host threads -- race and give
+ * undefined results.  Errors: SP_ERR_PARAM (a limit above exceeded, invalid
+ * parameters, misaligned pointer), SP_ERR_CUDA; returns
+ * SP_WARN_THETA_BELOW_INIT like sp_detect_async. */
+SP_API int sp_detect_noalloc(const sp_params* p, const uint8_t* dev_seav, const uint32_t* dev_ldca,
+                             uint32_t threshold, sp_candidate* dev_out, uint32_t cap,
+                             uint32_t* dev_status, void* cuda_stream);
+
 /* Human-readable name of a status code (static storage). */
 SP_API const char* sp_strerror(int code);
 

@@ -32,13 +32,15 @@ SP_ERR_NOMEM = -8
 SP_ERR_STATE = -9
 SP_FLAG_SATURATED = 1
 SP_SCAN_AUTO, SP_SCAN_DIRECT, SP_SCAN_BINNED = 0, 1, 2
+SP_NOALLOC_MAX_RESULTS = 65536
+SP_NOALLOC_MAX_K_LOG2 = 12
 
 EXPORTED = (
     "sp_version", "sp_strerror", "sp_default_params", "sp_check_params", "sp_sketch_bytes",
     "sp_tau", "sp_z_theta", "sp_create", "sp_destroy", "sp_set_stream", "sp_get_params",
     "sp_reset", "sp_update", "sp_update_host", "sp_update_batched", "sp_merge",
     "sp_detect_async", "sp_results", "sp_detect", "sp_results_device", "sp_slide",
-    "sp_export", "sp_import",
+    "sp_export", "sp_import", "sp_detect_noalloc",
 )
 
 
@@ -93,6 +95,7 @@ def _load():
         "sp_slide": (i32, [vp, u32]),
         "sp_export": (i32, [vp, u32, vp, u64, P(u64)]),
         "sp_import": (i32, [vp, u32, vp, u64]),
+        "sp_detect_noalloc": (i32, [P(sp_params), vp, vp, u32, vp, u32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
