@@ -92,7 +92,7 @@ extern "C" {
  * max_join bounds the LPs that reach the LDCA test in one detect (0 = 1 << 26).
  * scan_mode selects how the LDCA bits of a scan reach memory (results are
  * identical): SP_SCAN_AUTO (0) picks the binned form for updates of at least
- * 2^22 pairs when it applies (k <= 4096, LC >= 32, lr * LC <= 2^20), else the
+ * 2^22 pairs when it applies (k <= 2048, LC >= 32, lr * LC <= 2^20), else the
  * direct form; SP_SCAN_DIRECT (1) sets every bit with an L2 atomic OR;
  * SP_SCAN_BINNED (2) sorts the pairs by LDC bit position, sets the bits of
  * each bit plane with shared-memory atomics and folds the planes into the
@@ -220,7 +220,9 @@ SP_API int sp_detect_async(sp_ctx* ctx, uint32_t router, uint32_t threshold);
  * host_out (may be NULL when cap = 0).  Errors: SP_ERR_TRUNCATED when
  * *n_total > cap; SP_ERR_CANDIDATE_OVERFLOW when the device result buffer
  * (max_candidates) or the join bound (max_join) overflowed, in which case the
- * list is incomplete; SP_ERR_STATE when no detect was issued; SP_ERR_CUDA. */
+ * list is incomplete; SP_ERR_TIMEOUT when a scan kernel of this context gave
+ * up a bounded wait since the last check (the sketch is incomplete; no GPU
+ * hang is possible); SP_ERR_STATE when no detect was issued; SP_ERR_CUDA. */
 SP_API int sp_results(sp_ctx* ctx, sp_candidate* host_out, uint64_t cap, uint64_t* n_total);
 
 /* sp_detect_async followed by sp_results. */

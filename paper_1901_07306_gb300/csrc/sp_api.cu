@@ -84,6 +84,7 @@ struct sp_ctx {
   uint64_t* keys = nullptr;                 // detect scratch: next_pow2(cap) keys
   sp_candidate* records = nullptr;          // sorted results, cap records
   DetectStatus* status = nullptr;
+  uint32_t* kerr = nullptr;                 // kernel error word (bounded waits)
   double* est_table = nullptr;              // -k ln(z / k), z = 0 .. k
   uint32_t cap = 0;
   bool detect_issued = false;
@@ -240,6 +241,7 @@ void sp_destroy(sp_ctx* ctx) {
   cudaFree(ctx->keys);
   cudaFree(ctx->records);
   cudaFree(ctx->status);
+  cudaFree(ctx->kerr);
   cudaFree(ctx->est_table);
   delete ctx;
 }
@@ -292,6 +294,7 @@ int sp_create(const sp_params* p, void* cuda_stream, sp_ctx** out) {
       cudaMalloc(&c->keys, key_slots * sizeof(uint64_t)) != cudaSuccess ||
       cudaMalloc(&c->records, (uint64_t)c->cap * sizeof(sp_candidate)) != cudaSuccess ||
       cudaMalloc(&c->status, sizeof(DetectStatus)) != cudaSuccess ||
+      cudaMalloc(&c->kerr, sizeof(uint32_t)) != cudaSuccess ||
       cudaMalloc(&c->est_table, ((1ull << p->k_log2) + 1) * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     rc = SP_ERR_NOMEM;
@@ -310,6 +313,7 @@ int sp_create(const sp_params* p, void* cuda_stream, sp_ctx** out) {
   }
   if (rc == SP_OK && sp::launch_zero(c->sketches, c->stride * p->n_routers, c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
   if (rc == SP_OK && cudaMemsetAsync(c->status, 0, sizeof(DetectStatus), c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
+  if (rc == SP_OK && cudaMemsetAsync(c->kerr, 0, sizeof(uint32_t), c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
   if (rc == SP_OK) {
     c->scan_grid = sp::scan_grid(d);
     c->planes = static_cast<uint32_t**>(calloc(p->n_routers, sizeof(uint32_t*)));
@@ -360,7 +364,10 @@ static int ensure_binned(sp_ctx* ctx, uint32_t router) {
     ctx->bs.max_pairs = kBinnedRoundPairs;
     ctx->bs.fold_grid = sp::binned_fold_grid();
     const uint32_t bins = 1u << ctx->p.k_log2;
-    const uint64_t cap = sp::binned_list_cap(ctx->bs.max_pairs, bins, ctx->bs.ctas);
+    // room for the largest round: max_pairs split into host staging chunks
+    const uint32_t chunks = (uint32_t)((ctx->bs.max_pairs + kStagingPairs - 1) / kStagingPairs);
+    const uint64_t cap = sp::binned_list_cap(ctx->bs.max_pairs, bins, ctx->bs.ctas, chunks);
+    if ((uint64_t)bins * ctx->bs.ctas * cap >= (1ull << 32)) return SP_ERR_PARAM;   // 32-bit list slots
     if (cudaMalloc(&ctx->bs.lists, (uint64_t)bins * ctx->bs.ctas * cap * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&ctx->bs.counts, (uint64_t)bins * ctx->bs.ctas * sizeof(uint32_t)) != cudaSuccess) {
       cudaGetLastError();
@@ -376,22 +383,30 @@ static int ensure_binned(sp_ctx* ctx, uint32_t router) {
   return SP_OK;
 }
 
+// Whether an update of n pairs takes the binned scan.
+static bool use_binned(const sp_ctx* ctx, uint64_t n_pairs) {
+  if (ctx->sliding || !sp::binned_applicable(ctx->d)) return false;
+  if (ctx->p.scan_mode == SP_SCAN_BINNED) return true;
+  return ctx->p.scan_mode == SP_SCAN_AUTO && n_pairs >= kBinnedMinPairs;
+}
+
+static sp::BinnedScratch binned_scratch(const sp_ctx* ctx, uint32_t router) {
+  sp::BinnedScratch s = ctx->bs;
+  s.planes = ctx->planes[router];
+  s.error = ctx->kerr;
+  s.accumulate = ctx->planes_dirty[router];
+  return s;
+}
+
 // One update of one router through the direct or the binned scan.
 static int do_update(sp_ctx* ctx, uint32_t router, const uint32_t* dev_pairs, uint64_t n_pairs) {
   if (ctx->sliding)
     return sp::launch_scan_stamp(ctx->d, ctx->st_seav(router), ctx->st_ldca(router), dev_pairs, n_pairs,
                                  ctx->slice_id(router), ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
-  bool binned = false;
-  if (sp::binned_applicable(ctx->d)) {
-    if (ctx->p.scan_mode == SP_SCAN_BINNED) binned = true;
-    else if (ctx->p.scan_mode == SP_SCAN_AUTO) binned = n_pairs >= kBinnedMinPairs;
-  }
-  if (binned) {
+  if (use_binned(ctx, n_pairs)) {
     int rc = ensure_binned(ctx, router);
     if (rc != SP_OK) return rc;
-    sp::BinnedScratch s = ctx->bs;
-    s.planes = ctx->planes[router];
-    s.accumulate = ctx->planes_dirty[router];
+    sp::BinnedScratch s = binned_scratch(ctx, router);
     if (sp::launch_scan_binned(ctx->d, ctx->seav(router), ctx->ldca(router), dev_pairs, n_pairs, s,
                                ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
     ctx->planes_dirty[router] = true;
@@ -446,25 +461,46 @@ int sp_update_host(sp_ctx* ctx, uint32_t router, const uint32_t* host_pairs, uin
   if (!host_pairs) return SP_ERR_PARAM;
   int rc = ensure_staging(ctx);
   if (rc != SP_OK) return rc;
-  // the copy stream must not overtake work already queued on the main stream
-  // that still reads a staging buffer: ev_free[b] marks the last scan of b
+  const bool binned = use_binned(ctx, n_pairs);
+  if (binned && (rc = ensure_binned(ctx, router)) != SP_OK) return rc;
+  const uint32_t bins = 1u << ctx->p.k_log2;
+  // Chunks of the host stream go through two device staging buffers: the copy
+  // of chunk j + 1 (copy stream) overlaps the scan of chunk j (main stream);
+  // ev_free[b] marks the last scan that reads buffer b.  A binned update bins
+  // every chunk of a round into the same lists and applies them once.
   uint64_t done = 0;
   uint32_t j = 0;
   while (done < n_pairs) {
-    const uint32_t b = j & 1u;
-    const uint64_t m = (n_pairs - done) < kStagingPairs ? (n_pairs - done) : kStagingPairs;
-    if (j >= 2 || ctx->ev_free[b]) {
-      if (cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[b], 0) != cudaSuccess) return SP_ERR_CUDA;
+    const uint64_t round_n = binned ? ((n_pairs - done) < ctx->bs.max_pairs ? (n_pairs - done) : ctx->bs.max_pairs)
+                                    : (n_pairs - done);
+    const uint32_t chunks = (uint32_t)((round_n + kStagingPairs - 1) / kStagingPairs);
+    const uint32_t cap = binned ? sp::binned_list_cap(round_n, bins, ctx->bs.ctas, chunks) : 0u;
+    const sp::BinnedScratch s = binned ? binned_scratch(ctx, router) : sp::BinnedScratch();
+    uint64_t rdone = 0, rot = 0;
+    for (uint32_t c = 0; rdone < round_n; ++c, ++j) {
+      const uint32_t b = j & 1u;
+      const uint64_t m = (round_n - rdone) < kStagingPairs ? (round_n - rdone) : kStagingPairs;
+      const uint32_t* src = host_pairs + 2 * (done + rdone);
+      if (cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[b], 0) != cudaSuccess ||
+          cudaMemcpyAsync(ctx->staging[b], src, m * 8, cudaMemcpyHostToDevice, ctx->copy_stream) != cudaSuccess ||
+          cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream) != cudaSuccess ||
+          cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[b], 0) != cudaSuccess) return SP_ERR_CUDA;
+      if (binned) {
+        if (sp::binned_bin_chunk(ctx->d, ctx->seav(router), ctx->ldca(router), ctx->staging[b], m, s, cap, c > 0,
+                                 (uint32_t)(rot % ctx->bs.ctas), ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+        rot += (m + sp::binned_tile_pairs() - 1) / sp::binned_tile_pairs();
+      } else if ((rc = do_update(ctx, router, ctx->staging[b], m)) != SP_OK) {
+        return rc;
+      }
+      if (cudaEventRecord(ctx->ev_free[b], ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+      rdone += m;
     }
-    if (cudaMemcpyAsync(ctx->staging[b], host_pairs + 2 * done, m * 8, cudaMemcpyHostToDevice,
-                        ctx->copy_stream) != cudaSuccess) return SP_ERR_CUDA;
-    if (cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream) != cudaSuccess) return SP_ERR_CUDA;
-    if (cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[b], 0) != cudaSuccess) return SP_ERR_CUDA;
-    rc = do_update(ctx, router, ctx->staging[b], m);
-    if (rc != SP_OK) return rc;
-    if (cudaEventRecord(ctx->ev_free[b], ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
-    done += m;
-    ++j;
+    if (binned) {
+      if (sp::binned_apply_round(ctx->d, s, cap, ctx->planes_dirty[router], ctx->stream) != cudaSuccess)
+        return SP_ERR_CUDA;
+      ctx->planes_dirty[router] = true;
+    }
+    done += round_n;
   }
   return SP_OK;
 }
@@ -536,8 +572,15 @@ int sp_results(sp_ctx* ctx, sp_candidate* host_out, uint64_t cap, uint64_t* n_to
   if (!ctx || !n_total || (cap && !host_out)) return SP_ERR_PARAM;
   if (!ctx->detect_issued) return SP_ERR_STATE;
   DetectStatus st;
+  uint32_t kerr = 0;
   if (cudaMemcpyAsync(&st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+      cudaMemcpyAsync(&kerr, ctx->kerr, sizeof(kerr), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+  if (kerr) {   // a scan kernel gave up a bounded wait: this window's sketch is incomplete
+    cudaMemsetAsync(ctx->kerr, 0, sizeof(uint32_t), ctx->stream);
+    *n_total = st.count;
+    return SP_ERR_TIMEOUT;
+  }
   *n_total = st.count;
   const uint64_t avail = st.count < ctx->cap ? st.count : ctx->cap;
   const uint64_t m = avail < cap ? avail : cap;

@@ -5,14 +5,17 @@
 // "plane b" the set of bit b of every LDC: LR x LC bits (32 KiB at k = 1024,
 // LR = 4, LC = 2^16).  A pair touches exactly one plane, so:
 //
-//  k_bin    (persistent, one 1024-thread block per SM) reads the pairs with
-//           coalesced 8-byte loads, does the SEAV update of Sec. 3.1-3.2 for
-//           sampled pairs (L2 RED, 1 pair in 2^tau), and counting-sorts each
-//           16K-pair tile by b in shared memory; each bin's run of hips is
-//           appended to the block's private list for that bin (no global
-//           atomics; lists[b][block][0 .. cap)).  A run that would overflow a
-//           list is applied directly with L2 REDs instead (any input is
-//           correct; only a skewed one is slower).
+//  k_bin    (persistent, one 1024-thread block per SM) streams 8K-pair tiles
+//           into shared memory with TMA bulk copies, double buffered (the next
+//           tile lands while this one is sorted; waits on the mbarrier are
+//           bounded and end in an error flag), does the SEAV update of
+//           Sec. 3.1-3.2 for sampled pairs (L2 RED, 1 pair in 2^tau), and
+//           counting-sorts each tile by b in shared memory; each bin's run of
+//           hips is appended to the block's private list for that bin, one
+//           thread per sorted position (no global atomics;
+//           lists[b][block][0 .. cap)).  A run that would overflow a list is
+//           applied directly with L2 REDs instead (any input is correct; only
+//           a skewed one is slower).
 //  k_apply  (one block per plane) starts the plane in shared memory from
 //           zero (or from the router's pending plane when earlier updates of
 //           the window have not been folded yet), sets bit (i, LH_i(hip)) for
@@ -24,7 +27,7 @@
 //           a 5-stage butterfly of warp shuffles transposes the 32 x 32 bit
 //           block, giving lane t the 32-bit word of LDC 32 J + t.
 //
-// Applicable when the bins are the LDC's k bit positions (k <= 4096) and one
+// Applicable when the bins are the LDC's k bit positions (k <= 2048) and one
 // plane fits in shared memory as whole words (LC >= 32, LR x LC <= 2^20 bits).
 #include <math.h>
 
@@ -35,9 +38,10 @@ namespace sp {
 namespace {
 
 constexpr int kBinThreads = 1024;
-constexpr int kTile = 16384;                       // pairs per block iteration
-constexpr int kPerThread = kTile / kBinThreads;    // 16
+constexpr int kTile = 8192;                        // pairs per block iteration
+constexpr int kPerThread = kTile / kBinThreads;    // 8
 constexpr int kApplyThreads = 512;
+constexpr int kApplyUnroll = 8;                    // hip loads in flight per lane
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
 __device__ __forceinline__ void seav_set(const DevParams& d, uint8_t* seav, uint32_t hip, uint32_t h1) {
@@ -98,36 +102,116 @@ __device__ void block_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t
   __syncthreads();
 }
 
+// ---- TMA 1D bulk copies into shared memory, completed on an mbarrier ------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One thread: arm the barrier for `bytes` and start the copy (16-byte aligned
+// source and destination, bytes a multiple of 16).
+__device__ __forceinline__ void tma_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               :: "r"(smem_addr(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+// Bounded wait for the barrier phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_addr(bar);
+  for (uint32_t it = 0; it < (1u << 20); ++it) {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(addr), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// k_bin: tiles of kTile pairs, tile (cta + i G) in iteration i.  Thread 0
+// prefetches tile i + 1 into the other raw buffer with one TMA bulk copy while
+// the block sorts tile i.  Tiles that are partial, or a stream that is not
+// 16-byte aligned, are read with plain loads instead.
 template <int LR>
 __global__ void __launch_bounds__(kBinThreads, 1)
 k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
       const uint32_t* __restrict__ pairs, uint64_t n_pairs,
-      uint32_t* __restrict__ lists, uint32_t* __restrict__ counts, uint32_t cap) {
-  extern __shared__ uint32_t smem[];
+      uint32_t* __restrict__ lists, uint32_t* __restrict__ counts, uint32_t cap,
+      uint32_t* __restrict__ error, bool append, uint32_t rot) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
   const uint32_t bins = 1u << d.k_log2;
-  uint32_t* s_count = smem;                 // per-tile count, then kept count
-  uint32_t* s_off = s_count + bins;         // per-tile exclusive offsets
-  uint32_t* s_cursor = s_off + bins;        // this block's fill of each list
-  uint32_t* s_sorted = s_cursor + bins;     // kTile hips sorted by bin
+  uint2* raw = reinterpret_cast<uint2*>(smem_raw);                     // [2][kTile]
+  uint32_t* s_sorted = reinterpret_cast<uint32_t*>(raw + 2 * kTile);    // [kTile]
+  uint32_t* s_pos = s_sorted + kTile;                                  // [kTile] list slot or ~0
+  uint32_t* s_count = s_pos + kTile;                                    // [bins] count, then kept
+  uint32_t* s_off = s_count + bins;                                     // [bins] tile offsets
+  uint32_t* s_cursor = s_off + bins;                                    // [bins] list fill
+  uint32_t* s_dst = s_cursor + bins;                                    // [bins] first free slot
   __shared__ uint32_t s_warp[32];
-  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  __shared__ __align__(8) uint64_t s_bar[2];
+  const uint32_t tid = threadIdx.x;
   const uint32_t G = gridDim.x, cta = blockIdx.x;
+  const uint32_t slot = (cta + rot) % G;          // which tiles this block takes
   const uint32_t tau_mask = (1u << d.tau) - 1u;
   const uint32_t h3_shift = 32u - d.k_log2;
-  for (uint32_t b = tid; b < bins; b += kBinThreads) { s_count[b] = 0; s_cursor[b] = 0; }
-  __syncthreads();
   const uint64_t n_tiles = (n_pairs + kTile - 1) / kTile;
+  const uint64_t n_full = n_pairs / kTile;
+  const bool use_tma = ((uintptr_t)pairs & 15u) == 0;
   const uint2* p2 = reinterpret_cast<const uint2*>(pairs);
-  for (uint64_t tile = cta; tile < n_tiles; tile += G) {
+  // appending continues this block's lists from an earlier chunk of the round
+  for (uint32_t b = tid; b < bins; b += kBinThreads) {
+    s_count[b] = 0;
+    s_cursor[b] = append ? counts[(uint64_t)b * G + cta] : 0u;
+  }
+  if (tid == 0) { mbar_init(&s_bar[0]); mbar_init(&s_bar[1]); }
+  __syncthreads();
+  // tile of iteration i, and whether it comes through TMA
+  auto tile_of = [&](uint64_t i) { return (uint64_t)slot + i * G; };
+  auto by_tma = [&](uint64_t tile) { return use_tma && tile < n_full; };
+  uint32_t uses[2] = {0u, 0u};                  // completed phases of each barrier
+  if (tid == 0 && tile_of(0) < n_tiles && by_tma(tile_of(0)))
+    tma_load(raw, p2 + tile_of(0) * kTile, kTile * 8u, &s_bar[0]);
+  for (uint64_t i = 0; tile_of(i) < n_tiles; ++i) {
+    const uint64_t tile = tile_of(i);
+    const uint32_t buf = (uint32_t)(i & 1u);
+    // prefetch the next tile into the other buffer (freed at the end of i - 1)
+    const uint64_t next = tile_of(i + 1);
+    if (tid == 0 && next < n_tiles && by_tma(next))
+      tma_load(raw + (buf ^ 1u) * kTile, p2 + next * kTile, kTile * 8u, &s_bar[buf ^ 1u]);
+    const bool full = by_tma(tile);
+    if (full) {
+      const bool ok = __syncthreads_and(mbar_wait(&s_bar[buf], uses[buf] & 1u));
+      uses[buf]++;
+      if (!ok) {
+        // give up: flag the error, let this block's copies in flight land
+        // (bounded again), publish empty lists and leave
+        if (tid == 0) {
+          atomicOr(error, 1u);
+          mbar_wait(&s_bar[buf], (uses[buf] - 1u) & 1u);
+          if (next < n_tiles && by_tma(next)) mbar_wait(&s_bar[buf ^ 1u], uses[buf ^ 1u] & 1u);
+        }
+        for (uint32_t b = tid; b < bins; b += kBinThreads) counts[(uint64_t)b * G + cta] = s_cursor[b];
+        return;
+      }
+    }
     const uint64_t base = tile * kTile;
+    const uint32_t tile_n = (uint32_t)((n_pairs - base) < (uint64_t)kTile ? (n_pairs - base) : kTile);
     uint32_t hip[kPerThread], key[kPerThread];      // key = bin << 14 | rank, ~0 = none
 #pragma unroll
     for (int q = 0; q < kPerThread; ++q) {
-      const uint64_t p = base + (uint64_t)q * kBinThreads + tid;
+      const uint32_t j = (uint32_t)q * kBinThreads + tid;
       key[q] = kFull;
       hip[q] = 0;
-      if (p < n_pairs) {
-        const uint2 v = __ldcs(p2 + p);
+      if (j < tile_n) {
+        const uint2 v = full ? raw[buf * kTile + j] : __ldcs(p2 + base + j);
         const uint32_t h1 = mas(d.ha[0], d.hb[0], v.y);
         if ((h1 & tau_mask) == 0u) seav_set(d, seav, v.x, h1);
         const uint32_t h3 = mas(d.ha[1], d.hb[1], v.y) >> h3_shift;
@@ -142,6 +226,7 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
       const uint32_t c = s_count[b], have = s_cursor[b];
       const uint32_t keep = have + c <= cap ? c : (cap - have);
       s_count[b] = keep;
+      s_dst[b] = (b * G + cta) * cap + have;     // list entries < 2^32 (host check)
       s_cursor[b] = have + keep;
     }
     __syncthreads();
@@ -149,18 +234,28 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
     for (int q = 0; q < kPerThread; ++q) {
       if (key[q] != kFull) {
         const uint32_t b = key[q] >> 14, rank = key[q] & 0x3FFFu;
-        if (rank < s_count[b]) s_sorted[s_off[b] + rank] = hip[q];
-        else ldca_red<LR>(d, ldca, hip[q], b);          // list full: apply in L2
+        // every position of the tile gets its list slot, or ~0 when the list
+        // is full (then the pair is applied in L2 right here)
+        const uint32_t pos = s_off[b] + rank;
+        s_sorted[pos] = hip[q];
+        if (rank < s_count[b]) {
+          s_pos[pos] = s_dst[b] + rank;
+        } else {
+          s_pos[pos] = kFull;
+          ldca_red<LR>(d, ldca, hip[q], b);
+        }
       }
     }
     __syncthreads();
-    // append each bin's run to list (b, cta), one warp per bin
-    for (uint32_t b = warp; b < bins; b += kBinThreads / 32) {
-      const uint32_t keep = s_count[b];
-      if (keep == 0) continue;
-      uint32_t* dst = lists + ((uint64_t)b * G + cta) * cap + (s_cursor[b] - keep);
-      const uint32_t* src = s_sorted + s_off[b];
-      for (uint32_t i = lane; i < keep; i += 32) dst[i] = src[i];
+    // one thread per sorted position: consecutive positions of a bin go to
+    // consecutive list slots
+#pragma unroll
+    for (int q = 0; q < kPerThread; ++q) {
+      const uint32_t j = (uint32_t)q * kBinThreads + tid;
+      if (j < tile_n) {
+        const uint32_t slot = s_pos[j];
+        if (slot != kFull) lists[slot] = s_sorted[j];
+      }
     }
     __syncthreads();
     for (uint32_t b = tid; b < bins; b += kBinThreads) s_count[b] = 0;
@@ -185,13 +280,23 @@ k_apply(DevParams d, const uint32_t* __restrict__ lists, const uint32_t* __restr
   for (uint32_t c = warp; c < G; c += nwarps) {
     const uint32_t n = counts[(uint64_t)b * G + c];
     const uint32_t* src = lists + ((uint64_t)b * G + c) * cap;
-    for (uint32_t i = lane; i < n; i += 32) {
-      const uint32_t hip = __ldcs(src + i);
+    for (uint32_t i0 = 0; i0 < n; i0 += 32 * kApplyUnroll) {
+      uint32_t hip[kApplyUnroll];
 #pragma unroll
-      for (int r = 0; r < LR; ++r) {
-        const uint32_t col = (uint32_t)((uint64_t)mas(d.ha[2 + r], d.hb[2 + r], hip) >> cshift);
-        const uint32_t bit = ((uint32_t)r << d.lc_log2) | col;
-        atomicOr(&s_plane[bit >> 5], 1u << (bit & 31u));
+      for (int u = 0; u < kApplyUnroll; ++u) {          // all loads first: kApplyUnroll in flight
+        const uint32_t i = i0 + (uint32_t)u * 32 + lane;
+        hip[u] = i < n ? __ldcs(src + i) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < kApplyUnroll; ++u) {
+        if (i0 + (uint32_t)u * 32 + lane < n) {
+#pragma unroll
+          for (int r = 0; r < LR; ++r) {
+            const uint32_t col = (uint32_t)((uint64_t)mas(d.ha[2 + r], d.hb[2 + r], hip[u]) >> cshift);
+            const uint32_t bit = ((uint32_t)r << d.lc_log2) | col;
+            atomicOr(&s_plane[bit >> 5], 1u << (bit & 31u));
+          }
+        }
       }
     }
   }
@@ -213,68 +318,97 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, uint32_t lane) {
 }
 
 // planes: [k][W] words (W = LR * LC / 32); ldca: [LR * LC][k / 32] words.
+// A warp task is 8 consecutive plane words J0 .. J0 + 7 (one 32-byte sector
+// of each plane it reads) times 4 consecutive LDC words: it transposes
+// 32 planes x 32 LDCs per word and ORs the result into the lanes' LDC lines.
 __global__ void __launch_bounds__(256)
 k_fold(const uint32_t* __restrict__ planes, uint32_t* __restrict__ ldca, uint32_t W, uint32_t k_log2) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t wpl = 1u << (k_log2 - 5u);                       // words per LDC
   const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t J = gwarp; J < W; J += nwarp) {
-    uint32_t* line = ldca + ((uint64_t)J * 32u + lane) * wpl;     // LDC 32 J + lane
-    for (uint32_t q0 = 0; q0 < wpl; q0 += 4) {
-      uint32_t acc[4];
+  const bool vec = (W & 7u) == 0 && wpl >= 4;
+  const uint64_t n_groups = (W + 7) / 8;
+  const uint32_t n_q = (wpl + 3) / 4;                              // groups of 4 LDC words
+  for (uint64_t t = gwarp; t < n_groups * n_q; t += nwarp) {
+    const uint64_t g = t / n_q;
+    const uint32_t J0 = (uint32_t)(g * 8);
+    const uint32_t nj = (W - J0) < 8u ? (W - J0) : 8u;
+    {
+      const uint32_t q0 = (uint32_t)(t % n_q) * 4u;
+      uint32_t x[4][8];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const uint32_t q = q0 + u;
-        const uint32_t x = q < wpl ? planes[((uint64_t)(q * 32u + lane)) * W + J] : 0u;
-        acc[u] = transpose32(x, lane);
+        const uint32_t* row = planes + (uint64_t)(q * 32u + lane) * W + J0;
+        if (vec) {
+          const uint4 a = *reinterpret_cast<const uint4*>(row);
+          const uint4 c = *reinterpret_cast<const uint4*>(row + 4);
+          x[u][0] = a.x; x[u][1] = a.y; x[u][2] = a.z; x[u][3] = a.w;
+          x[u][4] = c.x; x[u][5] = c.y; x[u][6] = c.z; x[u][7] = c.w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) x[u][j] = (q < wpl && (uint32_t)j < nj) ? row[j] : 0u;
+        }
       }
-      if (wpl >= 4) {
-        uint4 o = *reinterpret_cast<uint4*>(line + q0);
-        o.x |= acc[0]; o.y |= acc[1]; o.z |= acc[2]; o.w |= acc[3];
-        *reinterpret_cast<uint4*>(line + q0) = o;
-      } else {
-        for (uint32_t u = 0; u < wpl; ++u) line[q0 + u] |= acc[u];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if ((uint32_t)j >= nj) break;
+        uint32_t acc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = transpose32(x[u][j], lane);
+        uint32_t* line = ldca + ((uint64_t)(J0 + j) * 32u + lane) * wpl;
+        if (wpl >= 4) {
+          uint4 o = *reinterpret_cast<uint4*>(line + q0);
+          o.x |= acc[0]; o.y |= acc[1]; o.z |= acc[2]; o.w |= acc[3];
+          *reinterpret_cast<uint4*>(line + q0) = o;
+        } else {
+          for (uint32_t u = 0; u < wpl; ++u) line[u] |= acc[u];
+        }
       }
     }
   }
 }
 
 template <int LR>
-cudaError_t run_binned(const DevParams& d, uint8_t* seav, uint32_t* ldca, const uint32_t* pairs,
-                       uint64_t n_pairs, const BinnedScratch& s, cudaStream_t st) {
+cudaError_t bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const uint32_t* pairs, uint64_t n,
+                      const BinnedScratch& s, uint32_t cap, bool append, uint32_t rot, cudaStream_t st) {
   const uint32_t bins = 1u << d.k_log2;
-  const size_t bin_smem = (size_t)(3u * bins + kTile) * sizeof(uint32_t);
+  // raw[2][kTile] pairs, sorted hips, their list slots, 4 counters per bin
+  const size_t bin_smem = (size_t)2 * kTile * 8 + (size_t)kTile * 8 + (size_t)4 * bins * 4;
   cudaError_t e = cudaFuncSetAttribute(k_bin<LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
   if (e != cudaSuccess) return e;
+  k_bin<LR><<<s.ctas, kBinThreads, bin_smem, st>>>(d, seav, ldca, pairs, n, s.lists, s.counts, cap, s.error,
+                                                   append, rot);
+  return cudaGetLastError();
+}
+
+template <int LR>
+cudaError_t apply_round(const DevParams& d, const BinnedScratch& s, uint32_t cap, bool accumulate, cudaStream_t st) {
+  const uint32_t bins = 1u << d.k_log2;
   const uint32_t words = ((uint32_t)LR << d.lc_log2) >> 5;
   const size_t apply_smem = (size_t)words * sizeof(uint32_t);
-  e = cudaFuncSetAttribute(k_apply<LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_smem);
+  cudaError_t e = cudaFuncSetAttribute(k_apply<LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_smem);
   if (e != cudaSuccess) return e;
-  uint64_t done = 0;
-  bool accumulate = s.accumulate;
-  while (done < n_pairs) {
-    const uint64_t n = (n_pairs - done) < s.max_pairs ? (n_pairs - done) : s.max_pairs;
-    const uint32_t cap = binned_list_cap(n, bins, s.ctas);
-    k_bin<LR><<<s.ctas, kBinThreads, bin_smem, st>>>(d, seav, ldca, pairs + 2 * done, n, s.lists, s.counts, cap);
-    k_apply<LR><<<bins, kApplyThreads, apply_smem, st>>>(d, s.lists, s.counts, s.ctas, cap, s.planes, accumulate);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    accumulate = true;
-    done += n;
-  }
-  return cudaSuccess;
+  k_apply<LR><<<bins, kApplyThreads, apply_smem, st>>>(d, s.lists, s.counts, s.ctas, cap, s.planes, accumulate);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 bool binned_applicable(const DevParams& d) {
   const uint64_t plane_bits = (uint64_t)d.lr << d.lc_log2;
-  return d.k_log2 >= 5 && d.k_log2 <= 12 && d.lc_log2 >= 5 && plane_bits <= (1ull << 20);
+  return d.k_log2 >= 5 && d.k_log2 <= 11 && d.lc_log2 >= 5 && plane_bits <= (1ull << 20);
 }
 
-uint32_t binned_list_cap(uint64_t n_pairs, uint32_t bins, uint32_t ctas) {
-  const double m = (double)n_pairs / ((double)bins * ctas);
+// List capacity for a round of n_pairs split into `chunks` binning launches:
+// a block takes at most ceil(tiles / ctas) + 1 tiles per launch (the tile to
+// block mapping rotates between launches), spread over the bins; 8 standard
+// deviations plus 32 of headroom, so that only skewed inputs overflow.
+uint32_t binned_list_cap(uint64_t n_pairs, uint32_t bins, uint32_t ctas, uint32_t chunks) {
+  const uint64_t tiles = (n_pairs + kTile - 1) / kTile;
+  const uint64_t per_cta = (tiles + ctas - 1) / ctas + (chunks > 1 ? chunks : 1);
+  const double m = (double)(per_cta * kTile < n_pairs ? per_cta * kTile : n_pairs) / bins;
   uint64_t cap = (uint64_t)(m + 8.0 * sqrt(m + 1.0) + 32.0);
   cap = (cap + 7) & ~7ull;                                   // 32-byte list starts
   return (uint32_t)cap;
@@ -297,19 +431,52 @@ cudaError_t launch_fold(const DevParams& d, const uint32_t* planes, uint32_t* ld
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan_binned(const DevParams& d, uint8_t* seav, uint32_t* ldca, const uint32_t* pairs,
-                               uint64_t n_pairs, const BinnedScratch& s, cudaStream_t st) {
+cudaError_t binned_bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const uint32_t* pairs,
+                             uint64_t n_pairs, const BinnedScratch& s, uint32_t cap, bool append, uint32_t rot,
+                             cudaStream_t st) {
   if (n_pairs == 0) return cudaSuccess;
   switch (d.lr) {
-    case 1: return run_binned<1>(d, seav, ldca, pairs, n_pairs, s, st);
-    case 2: return run_binned<2>(d, seav, ldca, pairs, n_pairs, s, st);
-    case 3: return run_binned<3>(d, seav, ldca, pairs, n_pairs, s, st);
-    case 4: return run_binned<4>(d, seav, ldca, pairs, n_pairs, s, st);
-    case 5: return run_binned<5>(d, seav, ldca, pairs, n_pairs, s, st);
-    case 6: return run_binned<6>(d, seav, ldca, pairs, n_pairs, s, st);
-    case 7: return run_binned<7>(d, seav, ldca, pairs, n_pairs, s, st);
-    default: return run_binned<8>(d, seav, ldca, pairs, n_pairs, s, st);
+    case 1: return bin_chunk<1>(d, seav, ldca, pairs, n_pairs, s, cap, append, rot, st);
+    case 2: return bin_chunk<2>(d, seav, ldca, pairs, n_pairs, s, cap, append, rot, st);
+    case 3: return bin_chunk<3>(d, seav, ldca, pairs, n_pairs, s, cap, append, rot, st);
+    case 4: return bin_chunk<4>(d, seav, ldca, pairs, n_pairs, s, cap, append, rot, st);
+    case 5: return bin_chunk<5>(d, seav, ldca, pairs, n_pairs, s, cap, append, rot, st);
+    case 6: return bin_chunk<6>(d, seav, ldca, pairs, n_pairs, s, cap, append, rot, st);
+    case 7: return bin_chunk<7>(d, seav, ldca, pairs, n_pairs, s, cap, append, rot, st);
+    default: return bin_chunk<8>(d, seav, ldca, pairs, n_pairs, s, cap, append, rot, st);
   }
+}
+
+cudaError_t binned_apply_round(const DevParams& d, const BinnedScratch& s, uint32_t cap, bool accumulate,
+                               cudaStream_t st) {
+  switch (d.lr) {
+    case 1: return apply_round<1>(d, s, cap, accumulate, st);
+    case 2: return apply_round<2>(d, s, cap, accumulate, st);
+    case 3: return apply_round<3>(d, s, cap, accumulate, st);
+    case 4: return apply_round<4>(d, s, cap, accumulate, st);
+    case 5: return apply_round<5>(d, s, cap, accumulate, st);
+    case 6: return apply_round<6>(d, s, cap, accumulate, st);
+    case 7: return apply_round<7>(d, s, cap, accumulate, st);
+    default: return apply_round<8>(d, s, cap, accumulate, st);
+  }
+}
+
+uint32_t binned_tile_pairs() { return (uint32_t)kTile; }
+
+cudaError_t launch_scan_binned(const DevParams& d, uint8_t* seav, uint32_t* ldca, const uint32_t* pairs,
+                               uint64_t n_pairs, const BinnedScratch& s, cudaStream_t st) {
+  uint64_t done = 0;
+  bool accumulate = s.accumulate;
+  while (done < n_pairs) {
+    const uint64_t n = (n_pairs - done) < s.max_pairs ? (n_pairs - done) : s.max_pairs;
+    const uint32_t cap = binned_list_cap(n, 1u << d.k_log2, s.ctas, 1);
+    cudaError_t e = binned_bin_chunk(d, seav, ldca, pairs + 2 * done, n, s, cap, false, 0, st);
+    if (e == cudaSuccess) e = binned_apply_round(d, s, cap, accumulate, st);
+    if (e != cudaSuccess) return e;
+    accumulate = true;
+    done += n;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace sp

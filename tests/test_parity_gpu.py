@@ -184,7 +184,7 @@ def test_merge_parity(sp, torch, mode):
         assert_same_sketch(ctx, whole, router=4)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_update_host_double_buffer(sp, torch, mode):
     pairs = W.uniform_pairs((1 << 22) + 12345, seed=8, n_hosts=100000)   # > one staging buffer
     kw = dict(theta=1024, seed=8, scan_mode=mode)
