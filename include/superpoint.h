@@ -186,12 +186,45 @@ SP_API int sp_update(sp_ctx* ctx, uint32_t router, const uint32_t* dev_pairs, ui
  * Same semantics and errors as sp_update. */
 SP_API int sp_update_host(sp_ctx* ctx, uint32_t router, const uint32_t* host_pairs, uint64_t n_pairs);
 
-/* Batched scan: n_batches (router, pairs, n_pairs) triples of device streams
- * of uneven sizes are scanned by one persistent launch.  routers[b] may
- * repeat.  The three arrays are host arrays of n_batches entries.  Async.
- * Same per-batch semantics and errors as sp_update. */
+/* One batch of a batched scan: n_pairs pairs for one router (8-byte aligned
+ * device stream).  The device form of the table is read by the kernels. */
+typedef struct sp_batch {
+  const uint32_t* pairs;
+  uint64_t n_pairs;
+  uint32_t router;
+  uint32_t reserved;
+} sp_batch;
+
+/* Batched scan (the WPs of Sec. 4.1 fed together): n_batches
+ * (router, pairs, n_pairs) triples of device streams of uneven sizes, given as
+ * three host arrays; routers[b] may repeat.  Routers whose batches add up to
+ * at least 2^22 pairs take the binned scan (one binning launch per batch, one
+ * plane launch per router); all other batches are scanned by ONE persistent
+ * launch over a batch table, whose block shape comes from sp_autotune (or a
+ * default).  Same per-batch semantics and errors as sp_update.  Async; the
+ * table goes to the device through a context-owned pinned buffer, so the call
+ * is not valid inside a stream capture (SP_ERR_STATE): capture
+ * sp_update_batched_device instead. */
 SP_API int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
-                      const uint32_t* const* dev_pairs, const uint64_t* n_pairs);
+                             const uint32_t* const* dev_pairs, const uint64_t* n_pairs);
+
+/* Batched scan over a table that already lives in device memory
+ * (dev_batches[0 .. n_batches), n_batches <= 8192), always by the one
+ * persistent launch (direct form).  The kernel reads sizes and pointers when it
+ * runs, so a CUDA graph that captured this call can be replayed after the
+ * caller rewrites the table.  A batch whose router is out of range or whose
+ * stream is misaligned is skipped and makes the next sp_results return
+ * SP_ERR_ROUTER.  Not valid for sliding contexts (SP_ERR_STATE).  Async. */
+SP_API int sp_update_batched_device(sp_ctx* ctx, const sp_batch* dev_batches, uint32_t n_batches);
+
+/* Autotuner of the batched launch: times every compiled block shape
+ * (128 / 256 / 512 threads) at 1, 2 and 4 blocks per SM (and the most that fit)
+ * on router 0 with the caller's sample stream dev_pairs[0 .. 2 n_pairs)
+ * (scanned repeatedly; router 0's sketch is reset afterwards), keeps the
+ * fastest for this context and reports it.  Synchronises the stream.
+ * Either output may be NULL. */
+SP_API int sp_autotune(sp_ctx* ctx, const uint32_t* dev_pairs, uint64_t n_pairs,
+                       uint32_t* best_threads, uint32_t* best_blocks);
 
 /* Global SEAV/LDCA of Sec. 4.2: dst |= src for every source router, bitwise
  * OR over both structures (the OR of the WPs' sketches equals the sketch of

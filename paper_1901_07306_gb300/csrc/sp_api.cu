@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "sp_internal.h"
 
@@ -103,6 +104,15 @@ struct sp_ctx {
   uint8_t* stamps = nullptr;                // n_routers * st_stride bytes
   uint64_t st_seav_pad = 0, st_stride = 0;
   uint64_t* slice = nullptr;                // current slice t of each router
+
+  // batched scan: batch table (pinned host copy and device copy), block shape
+  sp_batch* desc_host = nullptr;
+  sp_batch* desc_dev = nullptr;
+  uint32_t desc_cap = 0;
+  cudaEvent_t ev_desc = nullptr;            // the last table upload has left desc_host
+  bool desc_pending = false;
+  int multi_threads = 256;
+  int multi_grid = 0;
 
   uint8_t* st_seav(uint32_t router) const { return stamps + (uint64_t)router * st_stride; }
   uint8_t* st_ldca(uint32_t router) const { return stamps + (uint64_t)router * st_stride + st_seav_pad; }
@@ -234,6 +244,9 @@ void sp_destroy(sp_ctx* ctx) {
   }
   free(ctx->planes_dirty);
   free(ctx->slice);
+  if (ctx->desc_host) cudaFreeHost(ctx->desc_host);
+  cudaFree(ctx->desc_dev);
+  if (ctx->ev_desc) cudaEventDestroy(ctx->ev_desc);
   cudaFree(ctx->stamps);
   cudaFree(ctx->bs.lists);
   cudaFree(ctx->bs.counts);
@@ -316,6 +329,7 @@ int sp_create(const sp_params* p, void* cuda_stream, sp_ctx** out) {
   if (rc == SP_OK && cudaMemsetAsync(c->kerr, 0, sizeof(uint32_t), c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
   if (rc == SP_OK) {
     c->scan_grid = sp::scan_grid(d);
+    c->multi_grid = sp::multi_max_grid(c->multi_threads);
     c->planes = static_cast<uint32_t**>(calloc(p->n_routers, sizeof(uint32_t*)));
     c->planes_dirty = static_cast<bool*>(calloc(p->n_routers, sizeof(bool)));
     c->slice = static_cast<uint64_t*>(calloc(p->n_routers, sizeof(uint64_t)));
@@ -505,6 +519,46 @@ int sp_update_host(sp_ctx* ctx, uint32_t router, const uint32_t* host_pairs, uin
   return SP_OK;
 }
 
+static bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// Uploads n entries of the batch table through the pinned buffer.
+static int upload_table(sp_ctx* ctx, const sp_batch* tab, uint32_t n) {
+  if (n > ctx->desc_cap) {
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;   // old table no longer read
+    if (ctx->desc_host) cudaFreeHost(ctx->desc_host);
+    cudaFree(ctx->desc_dev);
+    ctx->desc_host = nullptr;
+    ctx->desc_dev = nullptr;
+    ctx->desc_cap = 0;
+    const uint32_t cap = n < 1024 ? 1024 : n;
+    if (cudaMallocHost(&ctx->desc_host, cap * sizeof(sp_batch)) != cudaSuccess ||
+        cudaMalloc(&ctx->desc_dev, cap * sizeof(sp_batch)) != cudaSuccess) { cudaGetLastError(); return SP_ERR_NOMEM; }
+    ctx->desc_cap = cap;
+    ctx->desc_pending = false;
+  }
+  if (!ctx->ev_desc && cudaEventCreateWithFlags(&ctx->ev_desc, cudaEventDisableTiming) != cudaSuccess) return SP_ERR_CUDA;
+  if (ctx->desc_pending && cudaEventSynchronize(ctx->ev_desc) != cudaSuccess) return SP_ERR_CUDA;
+  memcpy(ctx->desc_host, tab, n * sizeof(sp_batch));
+  if (cudaMemcpyAsync(ctx->desc_dev, ctx->desc_host, n * sizeof(sp_batch), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+      cudaEventRecord(ctx->ev_desc, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+  ctx->desc_pending = true;
+  return SP_OK;
+}
+
+static int launch_table(sp_ctx* ctx, const sp_batch* dev_tab, uint32_t n) {
+  constexpr uint32_t kMaxTable = 8192;
+  for (uint32_t i = 0; i < n; i += kMaxTable) {
+    const uint32_t m = (n - i) < kMaxTable ? (n - i) : kMaxTable;
+    if (sp::launch_scan_multi(ctx->d, ctx->sketches, ctx->stride, ctx->seav_pad, ctx->p.n_routers, dev_tab + i, m,
+                              ctx->kerr, ctx->multi_threads, ctx->multi_grid, ctx->stream) != cudaSuccess)
+      return SP_ERR_CUDA;
+  }
+  return SP_OK;
+}
+
 int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
                       const uint32_t* const* dev_pairs, const uint64_t* n_pairs) {
   if (!ctx) return SP_ERR_PARAM;
@@ -514,11 +568,116 @@ int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
     if (routers[b] >= ctx->p.n_routers) return SP_ERR_ROUTER;
     if (n_pairs[b] && (!dev_pairs[b] || ((uintptr_t)dev_pairs[b] & 7u))) return SP_ERR_PARAM;
   }
-  for (uint32_t b = 0; b < n_batches; ++b) {
-    int rc = sp_update(ctx, routers[b], dev_pairs[b], n_pairs[b]);
-    if (rc != SP_OK) return rc;
+  if (ctx->sliding) {                       // stamps carry the slice: per batch
+    for (uint32_t b = 0; b < n_batches; ++b) {
+      int rc = sp_update(ctx, routers[b], dev_pairs[b], n_pairs[b]);
+      if (rc != SP_OK) return rc;
+    }
+    return SP_OK;
   }
-  return SP_OK;
+  if (capturing(ctx->stream)) return SP_ERR_STATE;
+  std::vector<uint64_t> total(ctx->p.n_routers, 0);
+  for (uint32_t b = 0; b < n_batches; ++b) total[routers[b]] += n_pairs[b];
+  const uint32_t bins = 1u << ctx->p.k_log2;
+  std::vector<sp_batch> rest;
+  rest.reserve(n_batches);
+  for (uint32_t r = 0; r < ctx->p.n_routers; ++r) {
+    if (total[r] == 0) continue;
+    if (!use_binned(ctx, total[r])) {
+      for (uint32_t b = 0; b < n_batches; ++b)
+        if (routers[b] == r && n_pairs[b]) rest.push_back(sp_batch{dev_pairs[b], n_pairs[b], r, 0u});
+      continue;
+    }
+    int rc = ensure_binned(ctx, r);
+    if (rc != SP_OK) return rc;
+    // rounds of consecutive batches of router r, at most max_pairs each
+    std::vector<uint32_t> mine;
+    for (uint32_t b = 0; b < n_batches; ++b)
+      if (routers[b] == r && n_pairs[b]) mine.push_back(b);
+    size_t i = 0;
+    while (i < mine.size()) {
+      if (n_pairs[mine[i]] > ctx->bs.max_pairs) {          // a batch that is a round by itself
+        if ((rc = do_update(ctx, r, dev_pairs[mine[i]], n_pairs[mine[i]])) != SP_OK) return rc;
+        ++i;
+        continue;
+      }
+      size_t j = i;
+      uint64_t sum = 0;
+      while (j < mine.size() && sum + n_pairs[mine[j]] <= ctx->bs.max_pairs) sum += n_pairs[mine[j++]];
+      const uint32_t cap = sp::binned_list_cap(sum, bins, ctx->bs.ctas, (uint32_t)(j - i));
+      const sp::BinnedScratch s = binned_scratch(ctx, r);
+      uint64_t rot = 0;
+      for (size_t q = i; q < j; ++q) {
+        const uint32_t b = mine[q];
+        if (sp::binned_bin_chunk(ctx->d, ctx->seav(r), ctx->ldca(r), dev_pairs[b], n_pairs[b], s, cap, q > i,
+                                 (uint32_t)(rot % ctx->bs.ctas), ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+        rot += (n_pairs[b] + sp::binned_tile_pairs() - 1) / sp::binned_tile_pairs();
+      }
+      if (sp::binned_apply_round(ctx->d, s, cap, ctx->planes_dirty[r], ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+      ctx->planes_dirty[r] = true;
+      i = j;
+    }
+  }
+  if (rest.empty()) return SP_OK;
+  int rc = upload_table(ctx, rest.data(), (uint32_t)rest.size());
+  if (rc != SP_OK) return rc;
+  return launch_table(ctx, ctx->desc_dev, (uint32_t)rest.size());
+}
+
+int sp_update_batched_device(sp_ctx* ctx, const sp_batch* dev_batches, uint32_t n_batches) {
+  if (!ctx) return SP_ERR_PARAM;
+  if (ctx->sliding) return SP_ERR_STATE;
+  if (n_batches == 0) return SP_OK;
+  if (!dev_batches || n_batches > 8192) return SP_ERR_PARAM;
+  return launch_table(ctx, dev_batches, n_batches);
+}
+
+int sp_autotune(sp_ctx* ctx, const uint32_t* dev_pairs, uint64_t n_pairs, uint32_t* best_threads,
+                uint32_t* best_blocks) {
+  if (!ctx || !dev_pairs || n_pairs == 0 || ((uintptr_t)dev_pairs & 7u)) return SP_ERR_PARAM;
+  if (ctx->sliding) return SP_ERR_STATE;
+  const sp_batch one{dev_pairs, n_pairs, 0u, 0u};
+  int rc = upload_table(ctx, &one, 1);
+  if (rc != SP_OK) return rc;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SP_ERR_CUDA;
+  const int shapes[3] = {128, 256, 512};
+  float best = 1e30f;
+  int bt = ctx->multi_threads, bg = ctx->multi_grid;
+  for (int t : shapes) {
+    const int most = 2048 / t;
+    const int per[4] = {1, 2, 4, most};
+    for (int k = 0; k < 4; ++k) {
+      if (per[k] > most || (k == 3 && (most == 1 || most == 2 || most == 4))) continue;
+      ctx->multi_threads = t;
+      ctx->multi_grid = sms * per[k];
+      if ((rc = launch_table(ctx, ctx->desc_dev, 1)) != SP_OK) break;    // warm up
+      cudaEventRecord(e0, ctx->stream);
+      for (int it = 0; it < 3; ++it)
+        if ((rc = launch_table(ctx, ctx->desc_dev, 1)) != SP_OK) break;
+      cudaEventRecord(e1, ctx->stream);
+      float ms = 0.f;
+      if (rc != SP_OK || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = rc != SP_OK ? rc : SP_ERR_CUDA;
+        break;
+      }
+      if (ms < best) { best = ms; bt = t; bg = ctx->multi_grid; }
+    }
+    if (rc != SP_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->multi_threads = bt;
+  ctx->multi_grid = bg;
+  if (rc != SP_OK) return rc;
+  if (best_threads) *best_threads = (uint32_t)bt;
+  if (best_blocks) *best_blocks = (uint32_t)(bg / (sms ? sms : 1));
+  rc = sp_reset(ctx, 0);
+  if (rc == SP_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = SP_ERR_CUDA;
+  return rc;
 }
 
 int sp_merge(sp_ctx* ctx, const uint32_t* routers, uint32_t n, uint32_t dst_router) {
@@ -576,10 +735,12 @@ int sp_results(sp_ctx* ctx, sp_candidate* host_out, uint64_t cap, uint64_t* n_to
   if (cudaMemcpyAsync(&st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
       cudaMemcpyAsync(&kerr, ctx->kerr, sizeof(kerr), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
-  if (kerr) {   // a scan kernel gave up a bounded wait: this window's sketch is incomplete
+  if (kerr) {
+    // bit 0: a scan kernel gave up a bounded wait (the sketch is incomplete);
+    // bit 1: a device batch table named a bad router or stream (batch skipped)
     cudaMemsetAsync(ctx->kerr, 0, sizeof(uint32_t), ctx->stream);
     *n_total = st.count;
-    return SP_ERR_TIMEOUT;
+    return (kerr & 1u) ? SP_ERR_TIMEOUT : SP_ERR_ROUTER;
   }
   *n_total = st.count;
   const uint64_t avail = st.count < ctx->cap ? st.count : ctx->cap;

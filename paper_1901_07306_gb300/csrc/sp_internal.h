@@ -62,6 +62,7 @@ struct BinnedScratch {
   uint32_t* lists = nullptr;    // [bins][ctas][cap] hips
   uint32_t* counts = nullptr;   // [bins][ctas]
   uint32_t* planes = nullptr;   // [k][LR * LC / 32] plane-major accumulator of one router
+  uint32_t* error = nullptr;    // device word: bit 0 = a bounded wait timed out
   bool accumulate = false;      // planes hold earlier bits (load instead of zero)
   uint32_t ctas = 0;            // persistent binning blocks
   uint64_t max_pairs = 0;       // pairs per binning round the lists are sized for
@@ -73,8 +74,21 @@ cudaError_t launch_zero(void* dev, uint64_t bytes, cudaStream_t s);
 cudaError_t launch_scan(const DevParams& d, uint8_t* seav, uint32_t* ldca,
                         const uint32_t* pairs, uint64_t n_pairs, int grid, cudaStream_t s);
 int scan_grid(const DevParams& d);
+// batched direct scan over a device table of batches (sp_batch, include/superpoint.h)
+cudaError_t launch_scan_multi(const DevParams& d, uint8_t* sketches, uint64_t stride, uint64_t seav_pad,
+                              uint32_t n_routers, const sp_batch* desc, uint32_t n_batches, uint32_t* err,
+                              int threads, int grid, cudaStream_t s);
+int multi_max_grid(int threads);
 bool binned_applicable(const DevParams& d);
-uint32_t binned_list_cap(uint64_t n_pairs, uint32_t bins, uint32_t ctas);
+uint32_t binned_list_cap(uint64_t n_pairs, uint32_t bins, uint32_t ctas, uint32_t chunks);
+uint32_t binned_tile_pairs();
+// one binning launch over pairs[0, n) into the lists (append: continue them)
+cudaError_t binned_bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const uint32_t* pairs,
+                             uint64_t n_pairs, const BinnedScratch& s, uint32_t cap, bool append, uint32_t rot,
+                             cudaStream_t st);
+// the planes of the lists' hips (accumulate: on top of the pending planes)
+cudaError_t binned_apply_round(const DevParams& d, const BinnedScratch& s, uint32_t cap, bool accumulate,
+                               cudaStream_t st);
 int binned_ctas();
 int binned_fold_grid();
 // scan with the LDCA bits accumulated in s.planes (no fold)

@@ -81,7 +81,116 @@ int grid_for() {
   return sms * per_sm;
 }
 
+// ---- batched form: many (router, pairs) batches in one persistent launch ----
+//
+// The work unit is a chunk of kChunk pairs of one batch.  Every block scans
+// the batch table once into a shared prefix of chunk counts (a batch with a
+// router out of range or a misaligned stream counts 0 chunks and raises bit 1
+// of *err), then takes chunks g = block, block + grid, ... and finds each
+// chunk's batch by binary search.  Routers index the context's sketches.
+constexpr uint32_t kChunk = 2048;
+
+template <int LR, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+k_scan_multi(DevParams d, uint8_t* __restrict__ sketches, uint64_t stride, uint64_t seav_pad,
+             uint32_t n_routers, const sp_batch* __restrict__ desc, uint32_t n_batches,
+             uint32_t* __restrict__ err) {
+  extern __shared__ uint64_t s_pref[];                     // [n_batches + 1]
+  __shared__ uint64_t s_carry;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t tau_mask = (1u << d.tau) - 1u;
+  if (tid == 0) { s_carry = 0; s_pref[0] = 0; }
+  __syncthreads();
+  for (uint32_t base = 0; base < n_batches; base += THREADS) {
+    const uint32_t b = base + tid;
+    uint64_t c = 0;
+    if (b < n_batches) {
+      const sp_batch x = desc[b];
+      const bool ok = x.router < n_routers && (x.n_pairs == 0 || (x.pairs && ((uintptr_t)x.pairs & 7u) == 0));
+      if (!ok && blockIdx.x == 0) atomicOr(err, 2u);
+      c = ok ? (x.n_pairs + kChunk - 1) / kChunk : 0;
+    }
+    // inclusive block scan of c (THREADS <= 1024) through shared memory
+    __shared__ uint64_t s_tmp[1024];
+    s_tmp[tid] = c;
+    __syncthreads();
+    for (uint32_t o = 1; o < THREADS; o <<= 1) {
+      const uint64_t y = tid >= o ? s_tmp[tid - o] : 0;
+      __syncthreads();
+      s_tmp[tid] += y;
+      __syncthreads();
+    }
+    if (b < n_batches) s_pref[b + 1] = s_carry + s_tmp[tid];
+    __syncthreads();
+    if (tid == THREADS - 1) s_carry += s_tmp[tid];
+    __syncthreads();
+  }
+  const uint64_t total = s_pref[n_batches];
+  for (uint64_t g = blockIdx.x; g < total; g += gridDim.x) {
+    uint32_t lo = 0, hi = n_batches;                       // last b with s_pref[b] <= g
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (s_pref[mid] <= g) lo = mid; else hi = mid;
+    }
+    const sp_batch x = desc[lo];
+    const uint64_t start = (g - s_pref[lo]) * kChunk;
+    const uint32_t cnt = (uint32_t)((x.n_pairs - start) < kChunk ? (x.n_pairs - start) : kChunk);
+    uint8_t* seav = sketches + (uint64_t)x.router * stride;
+    uint32_t* ldca = reinterpret_cast<uint32_t*>(seav + seav_pad);
+    const uint2* p2 = reinterpret_cast<const uint2*>(x.pairs) + start;
+    for (uint32_t i = tid; i < cnt; i += THREADS) {
+      const uint2 v = __ldcs(p2 + i);
+      scan_pair<LR>(d, seav, ldca, v.x, v.y, tau_mask);
+    }
+  }
+}
+
+template <int LR>
+cudaError_t multi_lr(const DevParams& d, uint8_t* sketches, uint64_t stride, uint64_t seav_pad, uint32_t n_routers,
+                     const sp_batch* desc, uint32_t n_batches, uint32_t* err, int threads, int grid, cudaStream_t s) {
+  const size_t smem = ((size_t)n_batches + 1) * sizeof(uint64_t);
+  switch (threads) {
+    case 128:
+      cudaFuncSetAttribute(k_scan_multi<LR, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_scan_multi<LR, 128><<<grid, 128, smem, s>>>(d, sketches, stride, seav_pad, n_routers, desc, n_batches, err);
+      break;
+    case 512:
+      cudaFuncSetAttribute(k_scan_multi<LR, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_scan_multi<LR, 512><<<grid, 512, smem, s>>>(d, sketches, stride, seav_pad, n_routers, desc, n_batches, err);
+      break;
+    default:
+      cudaFuncSetAttribute(k_scan_multi<LR, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_scan_multi<LR, 256><<<grid, 256, smem, s>>>(d, sketches, stride, seav_pad, n_routers, desc, n_batches, err);
+      break;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_scan_multi(const DevParams& d, uint8_t* sketches, uint64_t stride, uint64_t seav_pad,
+                              uint32_t n_routers, const sp_batch* desc, uint32_t n_batches, uint32_t* err,
+                              int threads, int grid, cudaStream_t s) {
+  if (n_batches == 0) return cudaSuccess;
+  switch (d.lr) {
+    case 1: return multi_lr<1>(d, sketches, stride, seav_pad, n_routers, desc, n_batches, err, threads, grid, s);
+    case 2: return multi_lr<2>(d, sketches, stride, seav_pad, n_routers, desc, n_batches, err, threads, grid, s);
+    case 3: return multi_lr<3>(d, sketches, stride, seav_pad, n_routers, desc, n_batches, err, threads, grid, s);
+    case 4: return multi_lr<4>(d, sketches, stride, seav_pad, n_routers, desc, n_batches, err, threads, grid, s);
+    case 5: return multi_lr<5>(d, sketches, stride, seav_pad, n_routers, desc, n_batches, err, threads, grid, s);
+    case 6: return multi_lr<6>(d, sketches, stride, seav_pad, n_routers, desc, n_batches, err, threads, grid, s);
+    case 7: return multi_lr<7>(d, sketches, stride, seav_pad, n_routers, desc, n_batches, err, threads, grid, s);
+    default: return multi_lr<8>(d, sketches, stride, seav_pad, n_routers, desc, n_batches, err, threads, grid, s);
+  }
+}
+
+int multi_max_grid(int threads) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  per_sm = 2048 / threads;
+  return sms * per_sm;
+}
 
 int scan_grid(const DevParams& d) {
   switch (d.lr) {

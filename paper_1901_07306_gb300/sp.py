@@ -40,7 +40,7 @@ EXPORTED = (
     "sp_tau", "sp_z_theta", "sp_create", "sp_destroy", "sp_set_stream", "sp_get_params",
     "sp_reset", "sp_update", "sp_update_host", "sp_update_batched", "sp_merge",
     "sp_detect_async", "sp_results", "sp_detect", "sp_results_device", "sp_slide",
-    "sp_export", "sp_import", "sp_detect_noalloc",
+    "sp_export", "sp_import", "sp_detect_noalloc", "sp_update_batched_device", "sp_autotune",
 )
 
 
@@ -59,6 +59,16 @@ class sp_candidate(ctypes.Structure):
     _fields_ = [("ip", ctypes.c_uint32), ("z0", ctypes.c_uint32), ("est", ctypes.c_double),
                 ("flags", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
+
+class sp_batch(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_void_p), ("n_pairs", ctypes.c_uint64), ("router", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+# the same layout as a numpy record, for batch tables built on the host and
+# copied to device memory (sp_update_batched_device)
+BATCH = np.dtype([("pairs", "<u8"), ("n_pairs", "<u8"), ("router", "<u4"), ("reserved", "<u4")])
+assert BATCH.itemsize == ctypes.sizeof(sp_batch)
 
 CANDIDATE = np.dtype([("ip", "<u4"), ("z0", "<u4"), ("est", "<f8"), ("flags", "<u4"), ("pad", "<u4")])
 assert CANDIDATE.itemsize == ctypes.sizeof(sp_candidate)
@@ -96,6 +106,8 @@ def _load():
         "sp_export": (i32, [vp, u32, vp, u64, P(u64)]),
         "sp_import": (i32, [vp, u32, vp, u64]),
         "sp_detect_noalloc": (i32, [P(sp_params), vp, vp, u32, vp, u32, vp, vp]),
+        "sp_update_batched_device": (i32, [vp, vp, u32]),
+        "sp_autotune": (i32, [vp, vp, u64, P(u32), P(u32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -220,6 +232,22 @@ def sp_update_batched(ctx: int, routers, batches) -> None:
     for i, b in enumerate(batches):
         ptrs[i], ns[i] = _pairs_ptr(b)
     _check(lib.sp_update_batched(ctypes.c_void_p(ctx), nb, r, ptrs, ns), "sp_update_batched")
+
+
+def sp_update_batched_device(ctx: int, dev_table, n_batches: int) -> None:
+    """dev_table: device memory (tensor) holding n_batches BATCH records."""
+    ptr = dev_table.data_ptr() if hasattr(dev_table, "data_ptr") else int(dev_table)
+    _check(lib.sp_update_batched_device(ctypes.c_void_p(ctx), ctypes.c_void_p(ptr), n_batches),
+           "sp_update_batched_device")
+
+
+def sp_autotune(ctx: int, dev_pairs):
+    """Returns (threads, blocks per SM) chosen for the batched launch."""
+    ptr, n = _pairs_ptr(dev_pairs)
+    t, b = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib.sp_autotune(ctypes.c_void_p(ctx), ctypes.c_void_p(ptr), n, ctypes.byref(t), ctypes.byref(b)),
+           "sp_autotune")
+    return t.value, b.value
 
 
 def sp_merge(ctx: int, routers, dst_router: int) -> None:
