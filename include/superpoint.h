@@ -258,6 +258,16 @@ SP_API int sp_detect_async(sp_ctx* ctx, uint32_t router, uint32_t threshold);
  * hang is possible); SP_ERR_STATE when no detect was issued; SP_ERR_CUDA. */
 SP_API int sp_results(sp_ctx* ctx, sp_candidate* host_out, uint64_t cap, uint64_t* n_total);
 
+/* Non-blocking form of sp_results for pipelines: enqueues on the stream the
+ * copies of the last detect's status -- host_status[0] = super points found,
+ * host_status[1] = overflow flags (1: result buffer, 2: join bound) -- and of
+ * the first min(cap, max_candidates) result slots to host_out; only the first
+ * min(host_status[0], cap) of them are valid.  Pinned host memory makes the
+ * copies asynchronous; the caller waits on the stream (or an event) before
+ * reading.  Errors: SP_ERR_STATE when no detect was issued, SP_ERR_PARAM,
+ * SP_ERR_CUDA. */
+SP_API int sp_results_async(sp_ctx* ctx, sp_candidate* host_out, uint64_t cap, uint32_t* host_status);
+
 /* sp_detect_async followed by sp_results. */
 SP_API int sp_detect(sp_ctx* ctx, uint32_t router, uint32_t threshold,
               sp_candidate* host_out, uint64_t cap, uint64_t* n_total);

@@ -755,6 +755,17 @@ int sp_results(sp_ctx* ctx, sp_candidate* host_out, uint64_t cap, uint64_t* n_to
   return SP_OK;
 }
 
+int sp_results_async(sp_ctx* ctx, sp_candidate* host_out, uint64_t cap, uint32_t* host_status) {
+  if (!ctx || !host_status || (cap && !host_out)) return SP_ERR_PARAM;
+  if (!ctx->detect_issued) return SP_ERR_STATE;
+  const uint64_t m = cap < ctx->cap ? cap : ctx->cap;
+  if (cudaMemcpyAsync(host_status, ctx->status, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+    return SP_ERR_CUDA;
+  if (m && cudaMemcpyAsync(host_out, ctx->records, m * sizeof(sp_candidate), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+    return SP_ERR_CUDA;
+  return SP_OK;
+}
+
 int sp_detect(sp_ctx* ctx, uint32_t router, uint32_t threshold,
               sp_candidate* host_out, uint64_t cap, uint64_t* n_total) {
   int w = sp_detect_async(ctx, router, threshold);

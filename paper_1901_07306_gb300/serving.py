@@ -1,0 +1,240 @@
+"""Continuous-batching server for many watch points on one GPU.
+
+Routers (watch points, Sec. 4.1) send batches of <hip, oip> pairs; the
+server keeps every router's sketch resident in one library context, plus one
+extra router that plays the global server of Sec. 4.2.  All arithmetic runs
+in the library's kernels; this module only schedules.
+
+Engine (``SketchServer.run``):
+  * admission -- requests are admitted in arrival order while their bytes fit
+    a fixed device staging budget (``budget_bytes``); a request that does not
+    fit waits until earlier ones have been scanned and freed their room.
+  * continuous batching -- every engine step copies the newly admitted
+    requests host-to-device on a copy stream (pinned host memory), then scans
+    all of them with ONE ``sp_update_batched`` call on the compute stream;
+    while the GPU works on step s the host admits and copies step s + 1.
+  * windows -- every ``detect_every`` admitted pairs close a window (a time
+    slice): the routers are OR-merged into the global router, it is detected
+    asynchronously, and the routers start the next window (reset, or slide
+    when ``window_slices`` > 1, Sec. 5).  A request belongs to the window in
+    which it was admitted, so window contents depend only on arrival order.
+
+Latencies are host wall-clock times: ``ack`` = arrival to the moment its scan
+is seen complete; ``result`` = arrival to the moment the detection of its
+window is available on the host.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import sp
+
+
+@dataclass
+class Request:
+    router: int
+    pairs: torch.Tensor          # pinned host int32 tensor of 2 n values
+    arrival: float               # seconds after the start of the run
+    window: int = -1
+    t_ack: float = float("nan")
+    t_result: float = float("nan")
+
+    @property
+    def n_pairs(self) -> int:
+        return self.pairs.numel() // 2
+
+    @property
+    def nbytes(self) -> int:
+        return self.pairs.numel() * 4
+
+
+@dataclass
+class WindowResult:
+    index: int
+    n_pairs: int
+    records: np.ndarray = None
+    n_found: int = 0
+    t_ready: float = float("nan")
+
+
+class _Budget:
+    """Admission by a fixed device-memory budget: bytes of admitted requests
+    whose scan has not completed yet.  Device buffers come from PyTorch's
+    caching allocator and are released only after the scan that reads them
+    has been seen complete."""
+
+    def __init__(self, budget_bytes: int):
+        self.budget = int(budget_bytes)
+        self.in_use = 0
+
+    def fits(self, nbytes: int) -> bool:
+        if nbytes > self.budget:
+            raise ValueError(f"a {nbytes}-byte request exceeds the {self.budget}-byte budget")
+        return self.in_use + nbytes <= self.budget
+
+    def take(self, nbytes: int):
+        self.in_use += nbytes
+
+    def give(self, nbytes: int):
+        self.in_use -= nbytes
+
+
+class SketchServer:
+    """Routers 0 .. n_routers-1 plus the global router n_routers, one context.
+
+    batched=True is the continuous-batching engine described above;
+    batched=False is the plain path: every request is copied and scanned on
+    its own (one sp_update_host per request) as soon as it arrives, with the
+    same windows, so both paths produce the same detection results.
+    """
+
+    def __init__(self, n_routers: int, params: dict | None = None, budget_bytes: int = 1 << 30,
+                 detect_every: int = 1 << 24, window_slices: int = 1, max_step_requests: int = 1024,
+                 report_cap: int = 4096, batched: bool = True):
+        self.n_routers = n_routers
+        self.gs = n_routers                                  # the global server's router slot
+        kw = dict(params or {})
+        kw.update(n_routers=n_routers + 1, window_slices=window_slices)
+        self.compute = torch.cuda.Stream()
+        self.copy = torch.cuda.Stream()
+        self.ctx = sp.SuperPoint(sp.make_params(**kw), stream=self.compute)
+        self.budget = _Budget(budget_bytes)
+        self.detect_every = int(detect_every)
+        self.window_slices = window_slices
+        self.max_step = max_step_requests
+        self.report_cap = report_cap
+        self.batched = batched
+        self.windows: list[WindowResult] = []
+
+    def close(self):
+        self.ctx.close()
+
+    # -- window end: merge into the global router, detect, start the next ----
+    def _close_window(self, index: int, n_pairs: int):
+        c = self.ctx.ctx
+        with torch.cuda.stream(self.compute):
+            sp.sp_merge(c, list(range(self.n_routers)), self.gs)
+            sp.sp_detect_async(c, self.gs, 0)
+            out = np.zeros(self.report_cap, sp.CANDIDATE)
+            out_t = torch.from_numpy(out.view(np.uint8)).pin_memory()
+            status = torch.zeros(2, dtype=torch.int32).pin_memory()
+            sp.sp_results_async(c, out_t, self.report_cap, status)
+            for r in range(self.n_routers + 1):
+                if self.window_slices > 1:
+                    sp.sp_slide(c, r)
+                else:
+                    sp.sp_reset(c, r)
+            ev = torch.cuda.Event()
+            ev.record(self.compute)
+        return ev, WindowResult(index=index, n_pairs=n_pairs), out_t, status
+
+    def run(self, requests: list[Request]):
+        """Serves the requests (sorted by arrival); returns self.windows."""
+        from collections import deque
+        c = self.ctx.ctx
+        pending = deque(sorted(requests, key=lambda r: r.arrival))
+        steps = deque()           # (event, requests, device buffers, bytes)
+        detects = deque()         # (event, WindowResult, pinned records, pinned status, requests)
+        window, window_pairs, window_reqs = 0, 0, []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0  # noqa: E731
+        while pending or steps or detects:
+            progressed = False
+            while steps and steps[0][0].query():                     # scans done: ack, free
+                _, reqs, bufs, nbytes = steps.popleft()
+                t = now()
+                for r in reqs:
+                    r.t_ack = t
+                self.budget.give(nbytes)
+                progressed = True
+            while detects and detects[0][0].query():                 # detections on the host
+                _, res, out_t, status, reqs = detects.popleft()
+                t = now()
+                cnt, flags = (int(x) for x in status.numpy().view(np.uint32))
+                res.n_found = cnt
+                res.records = out_t.numpy().view(sp.CANDIDATE)[:min(cnt, self.report_cap)].copy()
+                res.t_ready = t
+                for r in reqs:
+                    r.t_result = t
+                self.windows.append(res)
+                progressed = True
+            # admit what has arrived, in order, within the budget and the window
+            step = []
+            boundary = False
+            while pending and pending[0].arrival <= now() and len(step) < self.max_step \
+                    and self.budget.fits(pending[0].nbytes):
+                r = pending.popleft()
+                self.budget.take(r.nbytes)                            # charged as it is admitted
+                r.window = window
+                window_pairs += r.n_pairs
+                window_reqs.append(r)
+                step.append(r)
+                if window_pairs >= self.detect_every:
+                    boundary = True
+                    break
+            if not pending and window_reqs and not step and not boundary:
+                boundary = True                                       # the last, partial window
+            if step:
+                nbytes = sum(r.nbytes for r in step)
+                if self.batched:
+                    with torch.cuda.stream(self.copy):
+                        bufs = [r.pairs.to("cuda", non_blocking=True) for r in step]
+                        copied = torch.cuda.Event()
+                        copied.record(self.copy)
+                    self.compute.wait_event(copied)
+                    with torch.cuda.stream(self.compute):
+                        for b in bufs:
+                            b.record_stream(self.compute)
+                        sp.sp_update_batched(c, [r.router for r in step], bufs)
+                else:
+                    bufs = []
+                    with torch.cuda.stream(self.compute):
+                        for r in step:                                # one copy + one launch each
+                            sp.sp_update_host(c, r.router, r.pairs)
+                ev = torch.cuda.Event()
+                ev.record(self.compute)
+                steps.append((ev, step, bufs, nbytes))
+                progressed = True
+            if boundary:
+                ev, res, out_t, status = self._close_window(window, window_pairs)
+                detects.append((ev, res, out_t, status, window_reqs))
+                window, window_pairs, window_reqs = window + 1, 0, []
+                progressed = True
+            if not progressed:
+                time.sleep(20e-6)
+        torch.cuda.synchronize()
+        self.elapsed = now()
+        return self.windows
+
+
+def poisson_requests(seed: int, n_routers: int, n_requests: int, rate_pairs_per_s: float,
+                     lo_log2: int = 12, hi_log2: int = 22, streams=None) -> list[Request]:
+    """Requests with log-uniform sizes in [2^lo, 2^hi] pairs, routers uniform,
+    Poisson arrivals whose mean pair rate is rate_pairs_per_s.  ``streams`` is
+    a callable (router, n, seed) -> uint32 pairs array, default uniform."""
+    from . import workloads as W
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(2.0 ** lo_log2), np.log(2.0 ** hi_log2), n_requests)).astype(np.int64)
+    routers = rng.integers(0, n_routers, n_requests)
+    gaps = rng.exponential(sizes.mean() / rate_pairs_per_s, n_requests)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    out = []
+    for i in range(n_requests):
+        n = int(sizes[i])
+        pairs = (streams(int(routers[i]), n, seed * 100003 + i) if streams is not None
+                 else W.uniform_pairs(n, seed=seed * 100003 + i, n_hosts=max(1, n // 4)))
+        t = torch.from_numpy(np.ascontiguousarray(pairs, np.uint32).reshape(-1).view(np.int32)).pin_memory()
+        out.append(Request(router=int(routers[i]), pairs=t, arrival=float(arrivals[i])))
+    return out
+
+
+def latency_summary(requests: list[Request]) -> dict:
+    ack = np.array([r.t_ack - r.arrival for r in requests])
+    res = np.array([r.t_result - r.arrival for r in requests])
+    return {"ack_ms": {"p50": float(np.percentile(ack, 50) * 1e3), "p99": float(np.percentile(ack, 99) * 1e3)},
+            "result_ms": {"p50": float(np.percentile(res, 50) * 1e3), "p99": float(np.percentile(res, 99) * 1e3)}}

@@ -41,6 +41,7 @@ EXPORTED = (
     "sp_reset", "sp_update", "sp_update_host", "sp_update_batched", "sp_merge",
     "sp_detect_async", "sp_results", "sp_detect", "sp_results_device", "sp_slide",
     "sp_export", "sp_import", "sp_detect_noalloc", "sp_update_batched_device", "sp_autotune",
+    "sp_results_async",
 )
 
 
@@ -108,6 +109,7 @@ def _load():
         "sp_detect_noalloc": (i32, [P(sp_params), vp, vp, u32, vp, u32, vp, vp]),
         "sp_update_batched_device": (i32, [vp, vp, u32]),
         "sp_autotune": (i32, [vp, vp, u64, P(u32), P(u32)]),
+        "sp_results_async": (i32, [vp, vp, u64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -272,6 +274,17 @@ def sp_results(ctx: int, cap: int | None = None):
     _check(rc, "sp_results", ok=(SP_OK, SP_ERR_TRUNCATED, SP_ERR_CANDIDATE_OVERFLOW))
     written = min(cap, n.value, sp_get_params(ctx).max_candidates)
     return out[:written], n.value, rc
+
+
+def _host_ptr(x) -> int:
+    return x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
+
+
+def sp_results_async(ctx: int, host_out, cap: int, host_status) -> None:
+    """host_out: pinned host buffer of >= cap CANDIDATE records (tensor or
+    array); host_status: pinned host buffer of 2 uint32/int32 words."""
+    _check(lib.sp_results_async(ctypes.c_void_p(ctx), ctypes.c_void_p(_host_ptr(host_out)), cap,
+                                ctypes.c_void_p(_host_ptr(host_status))), "sp_results_async")
 
 
 def sp_detect(ctx: int, router: int = 0, threshold: int = 0, cap: int | None = None):
