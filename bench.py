@@ -54,18 +54,25 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def scan_traffic_from_profile():
-    """dram bytes per scan launch from the committed ncu summary, or None when
-    the scan source changed since that capture."""
-    path = os.path.join(ROOT, "profiles", "k_scan_core_link.md")
-    src = os.path.join(ROOT, "paper_1901_07306_gb300", "csrc", "sp_scan.cu")
+def scan_source_hash():
+    h = hashlib.sha256()
+    for name in ("sp_scan.cu", "sp_scan_binned.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1901_07306_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def scan_traffic_from_profile(n_pairs):
+    """DRAM bytes (read + write) of one scan stage over n_pairs, scaled from
+    the committed ncu summary of a smaller case (traffic grows in proportion
+    to the pairs); None when the scan sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "scan_core_link_2e25.md")
     try:
         text = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        m_sha = re.search(r"scan_source_sha256_16:\s*([0-9a-f]{16})", text)
-        m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
-        if m_sha and m_b and m_sha.group(1) == sha:
-            return int(m_b.group(1))
+        m_sha = re.search(r"scan_sources_sha256_16:\s*([0-9a-f]{16})", text)
+        m_b = re.search(r"stage_dram_bytes:\s*([0-9]+)", text)
+        m_n = re.search(r"stage_pairs:\s*([0-9]+)", text)
+        if m_sha and m_b and m_n and m_sha.group(1) == scan_source_hash():
+            return int(int(m_b.group(1)) * n_pairs / int(m_n.group(1)))
     except Exception:
         pass
     return None
@@ -228,10 +235,8 @@ def run_ours(args):
     total_ms = t_start.elapsed_time(t_end)
     scan_ms = [e[0].elapsed_time(e[1]) for e in ev]
     det_ms = [e[2].elapsed_time(e[3]) for e in ev]
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    from paper_1901_07306_gb300 import exchange
+    total_ms = exchange.reduce_max(total_ms)
     recs, n_found, rc = sp.sp_results(c)
     found = set(recs["ip"].tolist())
     recall = len(found & set(planted.tolist())) / len(planted)
@@ -258,10 +263,7 @@ def run_ours(args):
             d2h = 16 + r.nbytes
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = exchange.reduce_max(dt)
         e2e = {"value": world * n * ke / dt, "unit": UNIT, "h2d_bytes_per_step": n * 8,
                "d2h_bytes_per_step": d2h, "steps": ke, "ms_per_step": 1e3 * dt / ke}
 
@@ -291,8 +293,9 @@ def run_ours(args):
                    "n_pairs": n, "threshold": theta, "profile": "D", "scan_mode": args.scan_mode,
                    "l2": "inputs larger than L2 (512 MiB of pairs per step vs 129 MB L2)",
                    "parallelism": f"{world} independent watch point(s), one per GPU"},
-        "roofline": {"kernel": "k_scan", "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": scan_traffic_from_profile(),
+        "roofline": {"kernel": ("scan stage k_bin + k_apply (binned)" if args.scan_mode != 1 else "k_scan (direct)"),
+                     "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": scan_traffic_from_profile(n),
                      "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                      "bytes_per_launch": n * SCAN_BYTES_PER_PAIR, "avg_launch_ms": scan_avg_ms},
         "scan_pairs_per_sec": n / (scan_avg_ms * 1e-3),
@@ -310,6 +313,188 @@ def run_ours(args):
     return 0
 
 
+# ---- the other workloads (printed as their own JSON lines) ----------------
+D3 = dict(r=16, isb=(0, 4, 8, 12), ibn=(7, 7, 7, 7), lc_log2=18)   # 16 routers x 2^24 pairs merged
+
+
+def _device_setup():
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1901_07306_gb300 import build as B
+    B.build()
+    from paper_1901_07306_gb300 import sp, workloads as W
+    return torch, sp, W
+
+
+def _timed(torch, fn, steps, warmup):
+    for _ in range(max(3, warmup)):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def run_distributed(args):
+    """16 simulated border routers, each 2^24 pairs arriving as uneven time-slice
+    batches; one step = reset, scan every batch, OR-merge into the global
+    router, detect.  Batched (one sp_update_batched call) vs one launch per
+    batch (sp_update per batch)."""
+    torch, sp, W = _device_setup()
+    n_routers, per = 16, 1 << args.router_log2
+    routers, sp_hosts = W.distributed(seed=3, n_per_router=per)
+    rng = np.random.default_rng(3)
+    batches = []
+    for r, pr in enumerate(routers):
+        w = np.exp(rng.uniform(0, np.log(16.0), args.batches_per_router))
+        cuts = np.floor(np.cumsum(w / w.sum())[:-1] * pr.shape[0]).astype(np.int64)
+        for part in np.split(pr, cuts):
+            batches.append((r, torch.from_numpy(np.ascontiguousarray(part).reshape(-1).view(np.int32)).cuda()))
+    order = rng.permutation(len(batches))
+    batches = [batches[i] for i in order]
+    total = sum(t.numel() // 2 for _, t in batches)
+    stream = torch.cuda.current_stream()
+    ctx = sp.SuperPoint(sp.make_params(theta=1024, seed=3, n_routers=n_routers + 1, **D3), stream=stream)
+    c = ctx.ctx
+    rlist, tlist = [r for r, _ in batches], [t for _, t in batches]
+
+    def step(batched):
+        for r in range(n_routers + 1):
+            sp.sp_reset(c, r)
+        if batched:
+            sp.sp_update_batched(c, rlist, tlist)
+        else:
+            for r, t in batches:
+                sp.sp_update(c, r, t)
+        sp.sp_merge(c, list(range(n_routers)), n_routers)
+        sp.sp_detect_async(c, n_routers, 1024)
+
+    ms_b = _timed(torch, lambda: step(True), args.steps, args.warmup)
+    res_b, n_b, _ = sp.sp_results(c)
+    ms_p = _timed(torch, lambda: step(False), max(3, args.steps // 4), 3)
+    res_p, n_p, _ = sp.sp_results(c)
+    assert np.array_equal(res_b, res_p), "batched and per-batch paths disagree"
+    recall = len(set(res_b["ip"].tolist()) & set(sp_hosts.tolist())) / len(sp_hosts)
+    line = {"metric": METRIC, "value": total / (ms_b * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"distributed: {n_routers} routers x 2^{args.router_log2} pairs from an overlapping "
+                                   "host population, 1,000 global super points split across routers, "
+                                   f"{args.batches_per_router} uneven batches per router; reset + scan + OR-merge + "
+                                   "detect per step; profile D3 (r=16, LC=2^18)",
+                       "n_pairs": total, "batches": len(batches)},
+            "plain_per_batch": {"value": total / (ms_p * 1e-3), "ms_per_step": ms_p},
+            "batched_speedup": ms_p / ms_b,
+            "super_points": {"found": int(n_b), "global_recall": recall}}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_sliding(args):
+    """A stream of time slices of lognormal size (2^28 pairs in 128 slices at
+    full size), window of 32 slices advanced one slice at a time (Sec. 5):
+    per slice = slide + scan the slice + detect the window."""
+    torch, sp, W = _device_setup()
+    T = args.slide_total_log2
+    scale = 1 << max(0, 28 - T)
+    sizes = W.slice_sizes(4, n_slices=128, total=1 << T, lo=(1 << 19) // scale, hi=(1 << 22) // scale)
+    slices, sp_hosts, sched = W.sliding_stream(seed=4, sizes=sizes, n_sp=64, sp_degree_per_slice=(64, 512))
+    dev_slices = [torch.from_numpy(x.reshape(-1).view(np.int32)).cuda() for x in slices]
+    stream = torch.cuda.current_stream()
+    k = 32
+    ctx = sp.SuperPoint(sp.make_params(theta=1024, seed=4, window_slices=k), stream=stream)
+    c = ctx.ctx
+
+    def one_pass(record):
+        sp.sp_reset(c, 0)
+        evs = []
+        for t, x in enumerate(dev_slices):
+            if t:
+                sp.sp_slide(c, 0)
+            sp.sp_update(c, 0, x)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sp.sp_detect_async(c, 0, 1024)
+            e1.record(stream)
+            evs.append((e0, e1))
+        return evs
+
+    one_pass(False)                                   # warm up
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    evs = one_pass(True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    det = sorted(e0.elapsed_time(e1) for e0, e1 in evs)
+    res, n_found, _ = sp.sp_results(c)
+    total = int(sizes.sum())
+    line = {"metric": METRIC, "value": total / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"sliding window: 2^{T} pairs in 128 lognormal slices "
+                                   f"[{int(sizes.min())}, {int(sizes.max())}] pairs, window {k} slices advanced one "
+                                   "slice at a time; per slice slide + scan + detect; profile D with slice stamps",
+                       "n_pairs": total, "slices": len(slices), "window_slices": k},
+            "detect_latency_ms": {"p50": det[len(det) // 2], "p99": det[min(len(det) - 1, int(0.99 * len(det)))]},
+            "super_points_last_window": int(n_found)}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving(args):
+    """64 routers sending batches of 2^12-2^22 pairs (log-uniform) with Poisson
+    arrivals; continuous batching under a 2 GiB staging budget vs the plain
+    one-launch-per-batch path, a detect every 2^24 global pairs."""
+    torch, sp, W = _device_setup()
+    from paper_1901_07306_gb300 import serving as S
+    n_routers = 64
+    reqs = S.poisson_requests(5, n_routers, args.requests, rate_pairs_per_s=1e13, lo_log2=12, hi_log2=22)
+    total = sum(r.n_pairs for r in reqs)
+
+    def serve(batched, rate):
+        mean = total / len(reqs)
+        rng = np.random.default_rng(55)
+        gaps = rng.exponential(mean / rate, len(reqs))
+        arr = np.cumsum(gaps) - gaps[0]
+        rs = [S.Request(router=r.router, pairs=r.pairs, arrival=float(a)) for r, a in zip(reqs, arr)]
+        srv = S.SketchServer(n_routers, dict(theta=1024, seed=5), budget_bytes=2 << 30, detect_every=1 << 24,
+                             batched=batched)
+        try:
+            wins = srv.run(rs)
+        finally:
+            srv.close()
+        return rs, wins, srv.elapsed
+
+    serve(True, 1e13)                                                # warm up (allocations, build)
+    rb, wb, tb = serve(True, 1e13)                                   # offered load above capacity
+    rp, wp, tp = serve(False, 1e13)
+    assert all(a.n_found == b.n_found and np.array_equal(a.records, b.records) for a, b in zip(wb, wp))
+    rate = 0.5 * total / tp                                          # half the plain path's capacity
+    lb, _, _ = serve(True, rate)
+    lp, _, _ = serve(False, rate)
+    line = {"metric": METRIC, "value": total / tb, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": tb * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"serving: {n_routers} routers, {len(reqs)} batches of 2^12-2^22 pairs "
+                                   "(log-uniform), Poisson arrivals, 2 GiB staging budget, detect every 2^24 "
+                                   "global pairs (OR-merge into a global router), profile D",
+                       "n_pairs": total, "windows": len(wb)},
+            "plain_per_batch": {"value": total / tp, "ms": tp * 1e3},
+            "latency_at_half_plain_capacity": {"offered_pairs_per_s": rate, "batched": S.latency_summary(lb),
+                                               "plain": S.latency_summary(lp)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -324,9 +509,21 @@ def main(argv=None):
     ap.add_argument("--ref-budget", type=float, default=60.0)
     ap.add_argument("--pairs-log2", type=int, default=26, help="window size (profiling captures use less)")
     ap.add_argument("--scan-mode", type=int, default=0, help="0 auto, 1 direct (L2 RED), 2 binned")
+    ap.add_argument("--workload", default="core_link",
+                    choices=["core_link", "distributed", "sliding", "serving"])
+    ap.add_argument("--router-log2", type=int, default=24)
+    ap.add_argument("--batches-per-router", type=int, default=64)
+    ap.add_argument("--slide-total-log2", type=int, default=28)
+    ap.add_argument("--requests", type=int, default=400)
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "distributed":
+        return run_distributed(args)
+    if args.workload == "sliding":
+        return run_sliding(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

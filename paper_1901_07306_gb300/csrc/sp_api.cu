@@ -500,8 +500,9 @@ int sp_update_host(sp_ctx* ctx, uint32_t router, const uint32_t* host_pairs, uin
           cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream) != cudaSuccess ||
           cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[b], 0) != cudaSuccess) return SP_ERR_CUDA;
       if (binned) {
-        if (sp::binned_bin_chunk(ctx->d, ctx->seav(router), ctx->ldca(router), ctx->staging[b], m, s, cap, c > 0,
-                                 (uint32_t)(rot % ctx->bs.ctas), ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+        if (sp::binned_bin_chunk(ctx->d, ctx->seav(router), ctx->ldca(router), sp::bin_src_one(ctx->staging[b], m), s,
+                                 cap, c > 0, (uint32_t)(rot % ctx->bs.ctas), ctx->stream) != cudaSuccess)
+          return SP_ERR_CUDA;
         rot += (m + sp::binned_tile_pairs() - 1) / sp::binned_tile_pairs();
       } else if ((rc = do_update(ctx, router, ctx->staging[b], m)) != SP_OK) {
         return rc;
@@ -604,14 +605,23 @@ int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
       size_t j = i;
       uint64_t sum = 0;
       while (j < mine.size() && sum + n_pairs[mine[j]] <= ctx->bs.max_pairs) sum += n_pairs[mine[j++]];
-      const uint32_t cap = sp::binned_list_cap(sum, bins, ctx->bs.ctas, (uint32_t)(j - i));
+      // the round's batches, up to kBinMaxSrc streams per binning launch
+      const uint32_t launches = (uint32_t)((j - i + sp::kBinMaxSrc - 1) / sp::kBinMaxSrc);
+      const uint32_t cap = sp::binned_list_cap(sum, bins, ctx->bs.ctas, launches);
       const sp::BinnedScratch s = binned_scratch(ctx, r);
       uint64_t rot = 0;
-      for (size_t q = i; q < j; ++q) {
-        const uint32_t b = mine[q];
-        if (sp::binned_bin_chunk(ctx->d, ctx->seav(r), ctx->ldca(r), dev_pairs[b], n_pairs[b], s, cap, q > i,
+      for (size_t q0 = i; q0 < j; q0 += sp::kBinMaxSrc) {
+        sp::BinSrc src{};
+        uint64_t tiles = 0;
+        for (size_t q = q0; q < j && q < q0 + sp::kBinMaxSrc; ++q) {
+          src.ptr[src.count] = dev_pairs[mine[q]];
+          src.n[src.count] = n_pairs[mine[q]];
+          tiles += (n_pairs[mine[q]] + sp::binned_tile_pairs() - 1) / sp::binned_tile_pairs();
+          ++src.count;
+        }
+        if (sp::binned_bin_chunk(ctx->d, ctx->seav(r), ctx->ldca(r), src, s, cap, q0 > i,
                                  (uint32_t)(rot % ctx->bs.ctas), ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
-        rot += (n_pairs[b] + sp::binned_tile_pairs() - 1) / sp::binned_tile_pairs();
+        rot += tiles;
       }
       if (sp::binned_apply_round(ctx->d, s, cap, ctx->planes_dirty[r], ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
       ctx->planes_dirty[r] = true;

@@ -57,6 +57,14 @@ __host__ __device__ __forceinline__ uint32_t gather_idx(uint32_t lp, uint32_t is
   return (uint32_t)(twice >> isb) & ((1u << ibn) - 1u);
 }
 
+// Up to kBinMaxSrc streams of one router, binned by one k_bin launch.
+constexpr int kBinMaxSrc = 32;
+struct BinSrc {
+  const uint32_t* ptr[kBinMaxSrc];
+  uint64_t n[kBinMaxSrc];
+  uint32_t count;
+};
+
 // Scratch of the binned scan (sp_scan_binned.cu), shared by a context's routers.
 struct BinnedScratch {
   uint32_t* lists = nullptr;    // [bins][ctas][cap] hips
@@ -83,9 +91,9 @@ bool binned_applicable(const DevParams& d);
 uint32_t binned_list_cap(uint64_t n_pairs, uint32_t bins, uint32_t ctas, uint32_t chunks);
 uint32_t binned_tile_pairs();
 // one binning launch over pairs[0, n) into the lists (append: continue them)
-cudaError_t binned_bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const uint32_t* pairs,
-                             uint64_t n_pairs, const BinnedScratch& s, uint32_t cap, bool append, uint32_t rot,
-                             cudaStream_t st);
+cudaError_t binned_bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const BinSrc& src,
+                             const BinnedScratch& s, uint32_t cap, bool append, uint32_t rot, cudaStream_t st);
+BinSrc bin_src_one(const uint32_t* pairs, uint64_t n_pairs);
 // the planes of the lists' hips (accumulate: on top of the pending planes)
 cudaError_t binned_apply_round(const DevParams& d, const BinnedScratch& s, uint32_t cap, bool accumulate,
                                cudaStream_t st);

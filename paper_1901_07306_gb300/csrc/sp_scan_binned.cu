@@ -143,8 +143,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 template <int LR>
 __global__ void __launch_bounds__(kBinThreads, 1)
 k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
-      const uint32_t* __restrict__ pairs, uint64_t n_pairs,
-      uint32_t* __restrict__ lists, uint32_t* __restrict__ counts, uint32_t cap,
+      BinSrc src, uint32_t* __restrict__ lists, uint32_t* __restrict__ counts, uint32_t cap,
       uint32_t* __restrict__ error, bool append, uint32_t rot) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const uint32_t bins = 1u << d.k_log2;
@@ -162,10 +161,23 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
   const uint32_t slot = (cta + rot) % G;          // which tiles this block takes
   const uint32_t tau_mask = (1u << d.tau) - 1u;
   const uint32_t h3_shift = 32u - d.k_log2;
-  const uint64_t n_tiles = (n_pairs + kTile - 1) / kTile;
-  const uint64_t n_full = n_pairs / kTile;
-  const bool use_tma = ((uintptr_t)pairs & 15u) == 0;
-  const uint2* p2 = reinterpret_cast<const uint2*>(pairs);
+  // tiles of the streams, back to back: stream b owns tiles [s_tpref[b], s_tpref[b + 1])
+  __shared__ uint64_t s_tpref[kBinMaxSrc + 1];
+  if (tid == 0) {
+    uint64_t acc = 0;
+    s_tpref[0] = 0;
+    for (uint32_t b = 0; b < src.count; ++b) {
+      acc += (src.n[b] + kTile - 1) / kTile;
+      s_tpref[b + 1] = acc;
+    }
+  }
+  __syncthreads();
+  const uint64_t n_tiles = s_tpref[src.count];
+  auto stream_of = [&](uint64_t tile) {       // the b with s_tpref[b] <= tile < s_tpref[b + 1]
+    uint32_t b = 0;
+    while (s_tpref[b + 1] <= tile) ++b;
+    return b;
+  };
   // appending continues this block's lists from an earlier chunk of the round
   for (uint32_t b = tid; b < bins; b += kBinThreads) {
     s_count[b] = 0;
@@ -175,17 +187,25 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
   __syncthreads();
   // tile of iteration i, and whether it comes through TMA
   auto tile_of = [&](uint64_t i) { return (uint64_t)slot + i * G; };
-  auto by_tma = [&](uint64_t tile) { return use_tma && tile < n_full; };
+  auto by_tma = [&](uint64_t tile) {           // a whole tile of a 16-byte aligned stream
+    const uint32_t b = stream_of(tile);
+    const uint64_t local = tile - s_tpref[b];
+    return ((uintptr_t)src.ptr[b] & 15u) == 0 && (local + 1) * kTile <= src.n[b];
+  };
+  auto tile_ptr = [&](uint64_t tile) {
+    const uint32_t b = stream_of(tile);
+    return reinterpret_cast<const uint2*>(src.ptr[b]) + (tile - s_tpref[b]) * kTile;
+  };
   uint32_t uses[2] = {0u, 0u};                  // completed phases of each barrier
   if (tid == 0 && tile_of(0) < n_tiles && by_tma(tile_of(0)))
-    tma_load(raw, p2 + tile_of(0) * kTile, kTile * 8u, &s_bar[0]);
+    tma_load(raw, tile_ptr(tile_of(0)), kTile * 8u, &s_bar[0]);
   for (uint64_t i = 0; tile_of(i) < n_tiles; ++i) {
     const uint64_t tile = tile_of(i);
     const uint32_t buf = (uint32_t)(i & 1u);
     // prefetch the next tile into the other buffer (freed at the end of i - 1)
     const uint64_t next = tile_of(i + 1);
     if (tid == 0 && next < n_tiles && by_tma(next))
-      tma_load(raw + (buf ^ 1u) * kTile, p2 + next * kTile, kTile * 8u, &s_bar[buf ^ 1u]);
+      tma_load(raw + (buf ^ 1u) * kTile, tile_ptr(next), kTile * 8u, &s_bar[buf ^ 1u]);
     const bool full = by_tma(tile);
     if (full) {
       const bool ok = __syncthreads_and(mbar_wait(&s_bar[buf], uses[buf] & 1u));
@@ -202,8 +222,10 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
         return;
       }
     }
-    const uint64_t base = tile * kTile;
-    const uint32_t tile_n = (uint32_t)((n_pairs - base) < (uint64_t)kTile ? (n_pairs - base) : kTile);
+    const uint32_t sb = stream_of(tile);
+    const uint64_t base = (tile - s_tpref[sb]) * kTile;                 // within stream sb
+    const uint32_t tile_n = (uint32_t)((src.n[sb] - base) < (uint64_t)kTile ? (src.n[sb] - base) : kTile);
+    const uint2* p2 = reinterpret_cast<const uint2*>(src.ptr[sb]);
     uint32_t hip[kPerThread], key[kPerThread];      // key = bin << 14 | rank, ~0 = none
 #pragma unroll
     for (int q = 0; q < kPerThread; ++q) {
@@ -371,14 +393,14 @@ k_fold(const uint32_t* __restrict__ planes, uint32_t* __restrict__ ldca, uint32_
 }
 
 template <int LR>
-cudaError_t bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const uint32_t* pairs, uint64_t n,
+cudaError_t bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const BinSrc& src,
                       const BinnedScratch& s, uint32_t cap, bool append, uint32_t rot, cudaStream_t st) {
   const uint32_t bins = 1u << d.k_log2;
   // raw[2][kTile] pairs, sorted hips, their list slots, 4 counters per bin
   const size_t bin_smem = (size_t)2 * kTile * 8 + (size_t)kTile * 8 + (size_t)4 * bins * 4;
   cudaError_t e = cudaFuncSetAttribute(k_bin<LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
   if (e != cudaSuccess) return e;
-  k_bin<LR><<<s.ctas, kBinThreads, bin_smem, st>>>(d, seav, ldca, pairs, n, s.lists, s.counts, cap, s.error,
+  k_bin<LR><<<s.ctas, kBinThreads, bin_smem, st>>>(d, seav, ldca, src, s.lists, s.counts, cap, s.error,
                                                    append, rot);
   return cudaGetLastError();
 }
@@ -431,19 +453,26 @@ cudaError_t launch_fold(const DevParams& d, const uint32_t* planes, uint32_t* ld
   return cudaGetLastError();
 }
 
-cudaError_t binned_bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const uint32_t* pairs,
-                             uint64_t n_pairs, const BinnedScratch& s, uint32_t cap, bool append, uint32_t rot,
-                             cudaStream_t st) {
-  if (n_pairs == 0) return cudaSuccess;
+BinSrc bin_src_one(const uint32_t* pairs, uint64_t n_pairs) {
+  BinSrc src{};
+  src.ptr[0] = pairs;
+  src.n[0] = n_pairs;
+  src.count = 1;
+  return src;
+}
+
+cudaError_t binned_bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const BinSrc& src,
+                             const BinnedScratch& s, uint32_t cap, bool append, uint32_t rot, cudaStream_t st) {
+  if (src.count == 0) return cudaSuccess;
   switch (d.lr) {
-    case 1: return bin_chunk<1>(d, seav, ldca, pairs, n_pairs, s, cap, append, rot, st);
-    case 2: return bin_chunk<2>(d, seav, ldca, pairs, n_pairs, s, cap, append, rot, st);
-    case 3: return bin_chunk<3>(d, seav, ldca, pairs, n_pairs, s, cap, append, rot, st);
-    case 4: return bin_chunk<4>(d, seav, ldca, pairs, n_pairs, s, cap, append, rot, st);
-    case 5: return bin_chunk<5>(d, seav, ldca, pairs, n_pairs, s, cap, append, rot, st);
-    case 6: return bin_chunk<6>(d, seav, ldca, pairs, n_pairs, s, cap, append, rot, st);
-    case 7: return bin_chunk<7>(d, seav, ldca, pairs, n_pairs, s, cap, append, rot, st);
-    default: return bin_chunk<8>(d, seav, ldca, pairs, n_pairs, s, cap, append, rot, st);
+    case 1: return bin_chunk<1>(d, seav, ldca, src, s, cap, append, rot, st);
+    case 2: return bin_chunk<2>(d, seav, ldca, src, s, cap, append, rot, st);
+    case 3: return bin_chunk<3>(d, seav, ldca, src, s, cap, append, rot, st);
+    case 4: return bin_chunk<4>(d, seav, ldca, src, s, cap, append, rot, st);
+    case 5: return bin_chunk<5>(d, seav, ldca, src, s, cap, append, rot, st);
+    case 6: return bin_chunk<6>(d, seav, ldca, src, s, cap, append, rot, st);
+    case 7: return bin_chunk<7>(d, seav, ldca, src, s, cap, append, rot, st);
+    default: return bin_chunk<8>(d, seav, ldca, src, s, cap, append, rot, st);
   }
 }
 
@@ -470,7 +499,7 @@ cudaError_t launch_scan_binned(const DevParams& d, uint8_t* seav, uint32_t* ldca
   while (done < n_pairs) {
     const uint64_t n = (n_pairs - done) < s.max_pairs ? (n_pairs - done) : s.max_pairs;
     const uint32_t cap = binned_list_cap(n, 1u << d.k_log2, s.ctas, 1);
-    cudaError_t e = binned_bin_chunk(d, seav, ldca, pairs + 2 * done, n, s, cap, false, 0, st);
+    cudaError_t e = binned_bin_chunk(d, seav, ldca, bin_src_one(pairs + 2 * done, n), s, cap, false, 0, st);
     if (e == cudaSuccess) e = binned_apply_round(d, s, cap, accumulate, st);
     if (e != cudaSuccess) return e;
     accumulate = true;

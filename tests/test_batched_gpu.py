@@ -172,3 +172,25 @@ def test_autotune_then_scan(sp, torch):
         for r in range(2):
             mine = [x for rr, x in zip(routers, data) if rr == r]
             assert same_sketch(ctx, O.Sketch(oparams(kw)).update(np.concatenate(mine)), r)
+
+
+def test_many_batches_of_one_router_binned(sp, torch):
+    """40 batches of one router (> 2^22 pairs in total): two binning launches
+    of up to 32 streams each append to the same lists; one stream starts 8
+    bytes off a 16-byte boundary (plain loads inside a TMA launch)."""
+    kw = dict(theta=256, seed=16, n_routers=2, scan_mode=0)
+    rng = np.random.default_rng(16)
+    sizes = rng.integers(60000, 180000, 40)
+    data = [W.uniform_pairs(int(n), seed=160 + i, n_hosts=20000) for i, n in enumerate(sizes)]
+    assert sum(sizes) >= (1 << 22)
+    tensors = [dev(torch, x) for x in data]
+    raw = torch.empty(2 * int(sizes[7]) + 2, dtype=torch.int32, device="cuda")
+    raw[2:].copy_(tensors[7])
+    tensors[7] = raw[2:]                                        # 8-byte aligned only
+    assert tensors[7].data_ptr() % 16 == 8
+    with sp.SuperPoint(**kw) as ctx:
+        sp.sp_update_batched(ctx.ctx, [1] * 40, tensors)
+        osk = O.Sketch(oparams(kw)).update(np.concatenate(data))
+        assert same_sketch(ctx, osk, 1)
+        seav, ldca = ctx.sketch_image(0)
+        assert not seav.any() and not ldca.any()
