@@ -264,8 +264,19 @@ def run_ours(args):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         dt = exchange.reduce_max(dt)
+        # context: the plain host-to-device copy rate of the same pinned buffer
+        scratch = torch.empty_like(dev_pairs)
+        scratch.copy_(host, non_blocking=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(5):
+            scratch.copy_(host, non_blocking=True)
+        torch.cuda.synchronize()
+        h2d = 5 * n * 8 / (time.perf_counter() - t1) / 1e9
+        del scratch
         e2e = {"value": world * n * ke / dt, "unit": UNIT, "h2d_bytes_per_step": n * 8,
-               "d2h_bytes_per_step": d2h, "steps": ke, "ms_per_step": 1e3 * dt / ke}
+               "d2h_bytes_per_step": d2h, "steps": ke, "ms_per_step": 1e3 * dt / ke,
+               "pinned_h2d_copy_gbs": h2d}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -315,6 +326,9 @@ def run_ours(args):
 
 # ---- the other workloads (printed as their own JSON lines) ----------------
 D3 = dict(r=16, isb=(0, 4, 8, 12), ibn=(7, 7, 7, 7), lc_log2=18)   # 16 routers x 2^24 pairs merged
+# serving windows of 2^24 pairs: a quarter of profile D's SEAs and LDCs keeps
+# its load per SE and per LDC (SEAV 2 MiB + LDCA 8 MiB per router)
+PROFILE_S = dict(r=12, isb=(0, 5, 10, 15), ibn=(7, 7, 7, 7), lc_log2=14)
 
 
 def _device_setup():
@@ -466,8 +480,8 @@ def run_serving(args):
         gaps = rng.exponential(mean / rate, len(reqs))
         arr = np.cumsum(gaps) - gaps[0]
         rs = [S.Request(router=r.router, pairs=r.pairs, arrival=float(a)) for r, a in zip(reqs, arr)]
-        srv = S.SketchServer(n_routers, dict(theta=1024, seed=5), budget_bytes=2 << 30, detect_every=1 << 24,
-                             batched=batched)
+        srv = S.SketchServer(n_routers, dict(PROFILE_S, theta=1024, seed=5), budget_bytes=2 << 30,
+                             detect_every=1 << 24, batched=batched)
         try:
             wins = srv.run(rs)
         finally:
@@ -486,7 +500,7 @@ def run_serving(args):
             "dtype": "u32", "data": "synthetic",
             "config": {"workload": f"serving: {n_routers} routers, {len(reqs)} batches of 2^12-2^22 pairs "
                                    "(log-uniform), Poisson arrivals, 2 GiB staging budget, detect every 2^24 "
-                                   "global pairs (OR-merge into a global router), profile D",
+                                   "global pairs (OR-merge into a global router), profile S (r=12, LC=2^14)",
                        "n_pairs": total, "windows": len(wb)},
             "plain_per_batch": {"value": total / tp, "ms": tp * 1e3},
             "latency_at_half_plain_capacity": {"offered_pairs_per_s": rate, "batched": S.latency_summary(lb),

@@ -105,12 +105,18 @@ struct sp_ctx {
   uint64_t st_seav_pad = 0, st_stride = 0;
   uint64_t* slice = nullptr;                // current slice t of each router
 
-  // batched scan: batch table (pinned host copy and device copy), block shape
-  sp_batch* desc_host = nullptr;
-  sp_batch* desc_dev = nullptr;
-  uint32_t desc_cap = 0;
-  cudaEvent_t ev_desc = nullptr;            // the last table upload has left desc_host
-  bool desc_pending = false;
+  // batched scan: a ring of batch tables (pinned host copy, device copy), so
+  // the host waits only for the upload issued kTableRing calls earlier
+  struct TableSlot {
+    sp_batch* host = nullptr;
+    sp_batch* dev = nullptr;
+    uint32_t cap = 0;
+    cudaEvent_t ev = nullptr;               // this slot's last upload has left `host`
+    bool pending = false;
+  };
+  static constexpr int kTableRing = 4;
+  TableSlot tables[kTableRing];
+  uint32_t table_next = 0;
   int multi_threads = 256;
   int multi_grid = 0;
 
@@ -244,9 +250,11 @@ void sp_destroy(sp_ctx* ctx) {
   }
   free(ctx->planes_dirty);
   free(ctx->slice);
-  if (ctx->desc_host) cudaFreeHost(ctx->desc_host);
-  cudaFree(ctx->desc_dev);
-  if (ctx->ev_desc) cudaEventDestroy(ctx->ev_desc);
+  for (auto& t : ctx->tables) {
+    if (t.host) cudaFreeHost(t.host);
+    cudaFree(t.dev);
+    if (t.ev) cudaEventDestroy(t.ev);
+  }
   cudaFree(ctx->stamps);
   cudaFree(ctx->bs.lists);
   cudaFree(ctx->bs.counts);
@@ -525,27 +533,30 @@ static bool capturing(cudaStream_t st) {
   return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
 }
 
-// Uploads n entries of the batch table through the pinned buffer.
-static int upload_table(sp_ctx* ctx, const sp_batch* tab, uint32_t n) {
-  if (n > ctx->desc_cap) {
-    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;   // old table no longer read
-    if (ctx->desc_host) cudaFreeHost(ctx->desc_host);
-    cudaFree(ctx->desc_dev);
-    ctx->desc_host = nullptr;
-    ctx->desc_dev = nullptr;
-    ctx->desc_cap = 0;
+// Uploads n entries of a batch table through the next pinned slot of the
+// ring; *dev receives the slot's device copy.
+static int upload_table(sp_ctx* ctx, const sp_batch* tab, uint32_t n, const sp_batch** dev) {
+  sp_ctx::TableSlot& t = ctx->tables[ctx->table_next++ % sp_ctx::kTableRing];
+  if (n > t.cap) {
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;   // old copy no longer read
+    if (t.host) cudaFreeHost(t.host);
+    cudaFree(t.dev);
+    t.host = nullptr;
+    t.dev = nullptr;
+    t.cap = 0;
+    t.pending = false;
     const uint32_t cap = n < 1024 ? 1024 : n;
-    if (cudaMallocHost(&ctx->desc_host, cap * sizeof(sp_batch)) != cudaSuccess ||
-        cudaMalloc(&ctx->desc_dev, cap * sizeof(sp_batch)) != cudaSuccess) { cudaGetLastError(); return SP_ERR_NOMEM; }
-    ctx->desc_cap = cap;
-    ctx->desc_pending = false;
+    if (cudaMallocHost(&t.host, cap * sizeof(sp_batch)) != cudaSuccess ||
+        cudaMalloc(&t.dev, cap * sizeof(sp_batch)) != cudaSuccess) { cudaGetLastError(); return SP_ERR_NOMEM; }
+    t.cap = cap;
   }
-  if (!ctx->ev_desc && cudaEventCreateWithFlags(&ctx->ev_desc, cudaEventDisableTiming) != cudaSuccess) return SP_ERR_CUDA;
-  if (ctx->desc_pending && cudaEventSynchronize(ctx->ev_desc) != cudaSuccess) return SP_ERR_CUDA;
-  memcpy(ctx->desc_host, tab, n * sizeof(sp_batch));
-  if (cudaMemcpyAsync(ctx->desc_dev, ctx->desc_host, n * sizeof(sp_batch), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
-      cudaEventRecord(ctx->ev_desc, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
-  ctx->desc_pending = true;
+  if (!t.ev && cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming) != cudaSuccess) return SP_ERR_CUDA;
+  if (t.pending && cudaEventSynchronize(t.ev) != cudaSuccess) return SP_ERR_CUDA;
+  memcpy(t.host, tab, n * sizeof(sp_batch));
+  if (cudaMemcpyAsync(t.dev, t.host, n * sizeof(sp_batch), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+      cudaEventRecord(t.ev, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+  t.pending = true;
+  *dev = t.dev;
   return SP_OK;
 }
 
@@ -629,9 +640,10 @@ int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
     }
   }
   if (rest.empty()) return SP_OK;
-  int rc = upload_table(ctx, rest.data(), (uint32_t)rest.size());
+  const sp_batch* dev_tab = nullptr;
+  int rc = upload_table(ctx, rest.data(), (uint32_t)rest.size(), &dev_tab);
   if (rc != SP_OK) return rc;
-  return launch_table(ctx, ctx->desc_dev, (uint32_t)rest.size());
+  return launch_table(ctx, dev_tab, (uint32_t)rest.size());
 }
 
 int sp_update_batched_device(sp_ctx* ctx, const sp_batch* dev_batches, uint32_t n_batches) {
@@ -647,7 +659,8 @@ int sp_autotune(sp_ctx* ctx, const uint32_t* dev_pairs, uint64_t n_pairs, uint32
   if (!ctx || !dev_pairs || n_pairs == 0 || ((uintptr_t)dev_pairs & 7u)) return SP_ERR_PARAM;
   if (ctx->sliding) return SP_ERR_STATE;
   const sp_batch one{dev_pairs, n_pairs, 0u, 0u};
-  int rc = upload_table(ctx, &one, 1);
+  const sp_batch* dev_tab = nullptr;
+  int rc = upload_table(ctx, &one, 1, &dev_tab);
   if (rc != SP_OK) return rc;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -664,10 +677,10 @@ int sp_autotune(sp_ctx* ctx, const uint32_t* dev_pairs, uint64_t n_pairs, uint32
       if (per[k] > most || (k == 3 && (most == 1 || most == 2 || most == 4))) continue;
       ctx->multi_threads = t;
       ctx->multi_grid = sms * per[k];
-      if ((rc = launch_table(ctx, ctx->desc_dev, 1)) != SP_OK) break;    // warm up
+      if ((rc = launch_table(ctx, dev_tab, 1)) != SP_OK) break;          // warm up
       cudaEventRecord(e0, ctx->stream);
       for (int it = 0; it < 3; ++it)
-        if ((rc = launch_table(ctx, ctx->desc_dev, 1)) != SP_OK) break;
+        if ((rc = launch_table(ctx, dev_tab, 1)) != SP_OK) break;
       cudaEventRecord(e1, ctx->stream);
       float ms = 0.f;
       if (rc != SP_OK || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {

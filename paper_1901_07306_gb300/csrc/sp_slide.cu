@@ -33,10 +33,6 @@ __device__ __forceinline__ uint32_t age_of(uint32_t stamp, uint32_t cur) {
   return cur >= stamp ? cur - stamp : cur + 255u - stamp;
 }
 
-__device__ __forceinline__ bool active(uint32_t stamp, uint32_t cur, uint32_t k) {
-  return stamp != 0u && age_of(stamp, cur) < k;
-}
-
 template <int LR>
 __device__ __forceinline__ void stamp_pair(const DevParams& d, uint8_t* __restrict__ st_seav,
                                            uint8_t* __restrict__ st_ldca, uint32_t hip, uint32_t oip,
@@ -77,25 +73,32 @@ k_scan_stamp(DevParams d, uint8_t* __restrict__ st_seav, uint8_t* __restrict__ s
 
 // stamps[lo, hi): reset those of age >= k (16 per uint4)
 __global__ void __launch_bounds__(kThreads)
+k_clean(uint4* __restrict__ st, uint64_t lo16, uint64_t hi16, uint32_t cur, uint32_t k);
+
+// Four stamps at once: byte j of the result is 0xFF iff byte j of s is an
+// active stamp (non-zero, age (cur - stamp) mod 255 below k).  Byte-wise
+// SIMD: d = cur - s mod 256, and age = d - 1 where cur < s (the mod-255 wrap).
+__device__ __forceinline__ uint32_t active_mask4(uint32_t s, uint32_t cur4, uint32_t k4) {
+  const uint32_t d = __vsub4(cur4, s);
+  const uint32_t age = __vadd4(d, __vcmpltu4(cur4, s));       // + 0xFF = - 1 where cur < s
+  return __vcmpltu4(age, k4) & ~__vcmpeq4(s, 0u);
+}
+
+// The same test as 4 bits (bit j for byte j): the four partial products of
+// the multiply land on distinct bits 21..24, so nothing carries.
+__device__ __forceinline__ uint32_t active4(uint32_t s, uint32_t cur4, uint32_t k4) {
+  return (((active_mask4(s, cur4, k4) & 0x01010101u) * 0x00204081u) >> 21) & 0xFu;
+}
+
+__global__ void __launch_bounds__(kThreads)
 k_clean(uint4* __restrict__ st, uint64_t lo16, uint64_t hi16, uint32_t cur, uint32_t k) {
+  const uint32_t cur4 = cur * 0x01010101u, k4 = k * 0x01010101u;
   for (uint64_t i = lo16 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi16;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    uint4 v = st[i];
-    uint32_t w[4] = {v.x, v.y, v.z, v.w};
-    bool changed = false;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      uint32_t out = 0;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const uint32_t s = (w[q] >> (8 * b)) & 0xFFu;
-        const uint32_t keep = (s != 0u && age_of(s, cur) < k) ? s : 0u;
-        changed |= keep != s;
-        out |= keep << (8 * b);
-      }
-      w[q] = out;
-    }
-    if (changed) st[i] = make_uint4(w[0], w[1], w[2], w[3]);
+    const uint4 v = st[i];
+    const uint4 o = make_uint4(v.x & active_mask4(v.x, cur4, k4), v.y & active_mask4(v.y, cur4, k4),
+                               v.z & active_mask4(v.z, cur4, k4), v.w & active_mask4(v.w, cur4, k4));
+    if (o.x != v.x || o.y != v.y || o.z != v.z || o.w != v.w) st[i] = o;
   }
 }
 
@@ -106,29 +109,16 @@ k_materialize(const uint2* __restrict__ st_seav, uint8_t* __restrict__ seav, uin
               uint32_t cur, uint32_t k) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t cur4 = cur * 0x01010101u, k4 = k * 0x01010101u;   // k <= 128 < 256
   for (uint64_t i = t0; i < seav_bytes; i += stride) {
-    const uint2 v = st_seav[i];
-    uint32_t m = 0;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      m |= (uint32_t)active((v.x >> (8 * b)) & 0xFFu, cur, k) << b;
-      m |= (uint32_t)active((v.y >> (8 * b)) & 0xFFu, cur, k) << (b + 4);
-    }
-    seav[i] = (uint8_t)m;
+    const uint2 v = __ldcs(st_seav + i);
+    seav[i] = (uint8_t)(active4(v.x, cur4, k4) | (active4(v.y, cur4, k4) << 4));
   }
   for (uint64_t i = t0; i < ldca_words; i += stride) {
-    uint32_t m = 0;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint4 v = st_ldca[2 * i + h];
-      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-          m |= (uint32_t)active((w[q] >> (8 * b)) & 0xFFu, cur, k) << (16 * h + 4 * q + b);
-    }
-    ldca[i] = m;
+    const uint4 a = __ldcs(st_ldca + 2 * i), b = __ldcs(st_ldca + 2 * i + 1);
+    ldca[i] = active4(a.x, cur4, k4) | (active4(a.y, cur4, k4) << 4) | (active4(a.z, cur4, k4) << 8) |
+              (active4(a.w, cur4, k4) << 12) | (active4(b.x, cur4, k4) << 16) | (active4(b.y, cur4, k4) << 20) |
+              (active4(b.z, cur4, k4) << 24) | (active4(b.w, cur4, k4) << 28);
   }
 }
 

@@ -40,6 +40,7 @@ class Request:
     pairs: torch.Tensor          # pinned host int32 tensor of 2 n values
     arrival: float               # seconds after the start of the run
     window: int = -1
+    _slot: object = None         # this request's slice of a staging arena
     t_ack: float = float("nan")
     t_result: float = float("nan")
 
@@ -103,6 +104,11 @@ class SketchServer:
         self.copy = torch.cuda.Stream()
         self.ctx = sp.SuperPoint(sp.make_params(**kw), stream=self.compute)
         self.budget = _Budget(budget_bytes)
+        # two staging arenas of half the budget each: step s fills arena s % 2
+        # and may reuse it once the scan of step s - 2 has completed
+        half = (int(budget_bytes) // 2) // 8 * 2             # int32 words, whole pairs
+        self.arenas = [torch.empty(half, dtype=torch.int32, device="cuda") for _ in range(2)] if batched else []
+        self.arena_free = [None, None]                        # event of the last step that read the arena
         self.detect_every = int(detect_every)
         self.window_slices = window_slices
         self.max_step = max_step_requests
@@ -140,6 +146,7 @@ class SketchServer:
         steps = deque()           # (event, requests, device buffers, bytes)
         detects = deque()         # (event, WindowResult, pinned records, pinned status, requests)
         window, window_pairs, window_reqs = 0, 0, []
+        steps_done_or_issued = []                 # one entry per issued step (its parity picks the arena)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0  # noqa: E731
@@ -150,6 +157,7 @@ class SketchServer:
                 t = now()
                 for r in reqs:
                     r.t_ack = t
+                    r._slot = None
                 self.budget.give(nbytes)
                 progressed = True
             while detects and detects[0][0].query():                 # detections on the host
@@ -166,9 +174,21 @@ class SketchServer:
             # admit what has arrived, in order, within the budget and the window
             step = []
             boundary = False
-            while pending and pending[0].arrival <= now() and len(step) < self.max_step \
+            arena = len(steps_done_or_issued) % 2 if self.batched else 0
+            arena_ready = not self.batched or self.arena_free[arena] is None or self.arena_free[arena].query()
+            used = 0
+            while arena_ready and pending and pending[0].arrival <= now() and len(step) < self.max_step \
                     and self.budget.fits(pending[0].nbytes):
-                r = pending.popleft()
+                r = pending[0]
+                if self.batched:
+                    words = r.pairs.numel()
+                    if words > self.arenas[arena].numel():
+                        raise ValueError(f"a {r.nbytes}-byte request exceeds half the staging budget")
+                    if used + words > self.arenas[arena].numel():
+                        break                                         # this step's arena is full
+                    r._slot = self.arenas[arena][used:used + words]
+                    used += words
+                pending.popleft()
                 self.budget.take(r.nbytes)                            # charged as it is admitted
                 r.window = window
                 window_pairs += r.n_pairs
@@ -183,13 +203,15 @@ class SketchServer:
                 nbytes = sum(r.nbytes for r in step)
                 if self.batched:
                     with torch.cuda.stream(self.copy):
-                        bufs = [r.pairs.to("cuda", non_blocking=True) for r in step]
+                        if self.arena_free[arena] is not None:
+                            self.copy.wait_event(self.arena_free[arena])
+                        for r in step:
+                            r._slot.copy_(r.pairs, non_blocking=True)
                         copied = torch.cuda.Event()
                         copied.record(self.copy)
                     self.compute.wait_event(copied)
+                    bufs = [r._slot for r in step]
                     with torch.cuda.stream(self.compute):
-                        for b in bufs:
-                            b.record_stream(self.compute)
                         sp.sp_update_batched(c, [r.router for r in step], bufs)
                 else:
                     bufs = []
@@ -198,7 +220,10 @@ class SketchServer:
                             sp.sp_update_host(c, r.router, r.pairs)
                 ev = torch.cuda.Event()
                 ev.record(self.compute)
+                if self.batched:
+                    self.arena_free[arena] = ev
                 steps.append((ev, step, bufs, nbytes))
+                steps_done_or_issued.append(None)
                 progressed = True
             if boundary:
                 ev, res, out_t, status = self._close_window(window, window_pairs)

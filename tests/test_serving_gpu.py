@@ -75,7 +75,7 @@ def test_windows_match_oracle_and_plain_path(serving):
 
 def test_budget_bounds_admission(serving):
     reqs = _requests(serving, seed=8, n=60, lo=10, hi=16, rate=1e12)   # everything arrives at once
-    budget = 1 << 20
+    budget = 2 << 20
     srv = serving.SketchServer(8, PARAMS, budget_bytes=budget, detect_every=1 << 40)
     seen = []
     orig_take = srv.budget.take
@@ -93,7 +93,7 @@ def test_budget_bounds_admission(serving):
     want, n, _ = _oracle_window(reqs, {0}, O.Params(**PARAMS))
     assert wins[0].n_found == n and np.array_equal(wins[0].records["ip"], want["ip"])
     with pytest.raises(ValueError):
-        srv2 = serving.SketchServer(2, PARAMS, budget_bytes=64)
+        srv2 = serving.SketchServer(2, PARAMS, budget_bytes=1024)
         try:
             srv2.run(_requests(serving, seed=9, n=2, lo=10, hi=11))
         finally:
