@@ -148,6 +148,21 @@ SP_API int sp_sketch_bytes(const sp_params* p, uint64_t* seav_bytes, uint64_t* l
 SP_API uint32_t sp_tau(uint32_t theta);
 SP_API uint32_t sp_z_theta(uint32_t k_log2, uint32_t threshold);
 
+/* Lemma 1 (Sec. 3.4): probability that a bit of a host's LDC union (the AND
+ * over the lr rows) is 1 when n_pairs distinct pairs are spread uniformly over
+ * the 2^lc_log2 columns of each row: (1 - (1 - 1/k)^(n / LC))^lr. */
+SP_API double sp_psu(uint64_t n_pairs, uint32_t k_log2, uint32_t lr, uint32_t lc_log2);
+
+/* LDCA sizing (Sec. 3.4, Lemma 1 and Theorem 1) for an expected n_pairs
+ * distinct pairs per window and a budget of ldc_budget LDCs of k = 2^k_log2
+ * bits: *lr and *lc_log2 receive the layout (lr in 1..8, LC a power of two,
+ * lr * LC <= ldc_budget, within the library limits) with the smallest Psu,
+ * fewer rows on ties; *psu its Psu; *lr_star Theorem 1's continuous optimum
+ * -V ln 2 / (n ln(1 - 1/k)) for V = ldc_budget.  Any output may be NULL.
+ * Errors: SP_ERR_PARAM (n_pairs = 0, k_log2 out of 5..16, ldc_budget = 0). */
+SP_API int sp_size_ldca(uint64_t n_pairs, uint32_t k_log2, uint64_t ldc_budget, uint32_t* lr,
+                        uint32_t* lc_log2, double* psu, double* lr_star);
+
 /* Creates a context on the current CUDA device.  cuda_stream is a
  * cudaStream_t (NULL = the legacy default stream); the context issues all
  * its work there.  Allocates and zeroes n_routers sketches plus scratch.

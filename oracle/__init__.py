@@ -88,6 +88,8 @@ def _load():
             "or_est": (ctypes.c_double, [u32, u32]),
             "or_z_theta": (u32, [u32, u32]),
             "or_detect": (ctypes.c_int, [PP, p, p, u32, p, u64, ctypes.POINTER(u64)]),
+            "or_psu": (ctypes.c_double, [ctypes.c_double, u32, ctypes.c_double, ctypes.c_double]),
+            "or_lr_star": (ctypes.c_double, [ctypes.c_double, u32, ctypes.c_double]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -198,6 +200,16 @@ def ldca_words(p: Params) -> int:
 
 def est(k_log2: int, z0: int) -> float:
     return _load().or_est(k_log2, z0)
+
+
+def psu(n_pairs: float, k_log2: int, lr: float, lc: float) -> float:
+    """Lemma 1."""
+    return _load().or_psu(float(n_pairs), k_log2, float(lr), float(lc))
+
+
+def lr_star(n_pairs: float, k_log2: int, v_ldcs: float) -> float:
+    """Theorem 1."""
+    return _load().or_lr_star(float(n_pairs), k_log2, float(v_ldcs))
 
 
 def z_theta(k_log2: int, theta: int) -> int:

@@ -369,3 +369,18 @@ int or_detect(const or_params *p, const uint8_t *seav, const uint32_t *ldca,
   free(found);
   return n_found > cap ? -1 : 0;
 }
+
+/* ---- Lemma 1 and Theorem 1 (Sec. 3.4): sizing the LDCA ----------------
+ * Psu: probability that a bit of a host's LDC union is 1 when N distinct
+ * pairs are spread over LC columns in each of LR rows.  LR*: the row count
+ * minimising Psu for a fixed number V = LR * LC of LDCs (continuous). */
+double or_psu(double n_pairs, uint32_t k_log2, double lr, double lc) {
+  double k = (double)((uint64_t)1 << k_log2);
+  double keep0 = pow(1.0 - 1.0 / k, n_pairs / lc);   /* a bit stays 0 in one LDC */
+  return pow(1.0 - keep0, lr);
+}
+
+double or_lr_star(double n_pairs, uint32_t k_log2, double v_ldcs) {
+  double k = (double)((uint64_t)1 << k_log2);
+  return -v_ldcs * log(2.0) / (n_pairs * log(1.0 - 1.0 / k));
+}

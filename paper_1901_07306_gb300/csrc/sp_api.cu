@@ -231,6 +231,35 @@ uint32_t sp_z_theta(uint32_t k_log2, uint32_t threshold) {
   return 0;
 }
 
+double sp_psu(uint64_t n_pairs, uint32_t k_log2, uint32_t lr, uint32_t lc_log2) {
+  const double k = (double)(1ull << k_log2);
+  const double zero_in_one_ldc = pow(1.0 - 1.0 / k, (double)n_pairs / (double)(1ull << lc_log2));
+  return pow(1.0 - zero_in_one_ldc, (double)lr);
+}
+
+int sp_size_ldca(uint64_t n_pairs, uint32_t k_log2, uint64_t ldc_budget, uint32_t* lr, uint32_t* lc_log2,
+                 double* psu, double* lr_star) {
+  if (n_pairs == 0 || k_log2 < 5 || k_log2 > 16 || ldc_budget == 0) return SP_ERR_PARAM;
+  double best = 2.0;
+  uint32_t best_lr = 1, best_c = 0;
+  for (uint32_t rows = 1; rows <= 8; ++rows) {
+    for (uint32_t c = 0; c <= 24; ++c) {
+      if ((uint64_t)rows << c > ldc_budget) break;
+      if (((uint64_t)rows << (c + k_log2)) > (1ull << 32)) break;
+      const double v = sp_psu(n_pairs, k_log2, rows, c);
+      if (v < best) { best = v; best_lr = rows; best_c = c; }
+    }
+  }
+  if (lr) *lr = best_lr;
+  if (lc_log2) *lc_log2 = best_c;
+  if (psu) *psu = best;
+  if (lr_star) {
+    const double k = (double)(1ull << k_log2);
+    *lr_star = -(double)ldc_budget * log(2.0) / ((double)n_pairs * log(1.0 - 1.0 / k));
+  }
+  return SP_OK;
+}
+
 void sp_destroy(sp_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);

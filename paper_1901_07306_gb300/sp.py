@@ -41,7 +41,7 @@ EXPORTED = (
     "sp_reset", "sp_update", "sp_update_host", "sp_update_batched", "sp_merge",
     "sp_detect_async", "sp_results", "sp_detect", "sp_results_device", "sp_slide",
     "sp_export", "sp_import", "sp_detect_noalloc", "sp_update_batched_device", "sp_autotune",
-    "sp_results_async",
+    "sp_results_async", "sp_psu", "sp_size_ldca",
 )
 
 
@@ -110,6 +110,8 @@ def _load():
         "sp_update_batched_device": (i32, [vp, vp, u32]),
         "sp_autotune": (i32, [vp, vp, u64, P(u32), P(u32)]),
         "sp_results_async": (i32, [vp, vp, u64, vp]),
+        "sp_psu": (ctypes.c_double, [u64, u32, u32, u32]),
+        "sp_size_ldca": (i32, [u64, u32, u64, P(u32), P(u32), P(ctypes.c_double), P(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -150,6 +152,19 @@ def make_params(r=14, isb=(0, 5, 10, 15), ibn=(7, 7, 7, 7), k_log2=10, lr=4, lc_
     p.n_routers, p.window_slices, p.max_candidates = n_routers, window_slices, max_candidates
     p.seed, p.max_join, p.scan_mode = seed & (2**64 - 1), max_join, scan_mode
     return p
+
+
+def sp_psu(n_pairs: int, k_log2: int, lr: int, lc_log2: int) -> float:
+    return lib.sp_psu(n_pairs, k_log2, lr, lc_log2)
+
+
+def sp_size_ldca(n_pairs: int, k_log2: int, ldc_budget: int):
+    """Returns (lr, lc_log2, psu, lr_star)."""
+    lr, c = ctypes.c_uint32(), ctypes.c_uint32()
+    psu, star = ctypes.c_double(), ctypes.c_double()
+    _check(lib.sp_size_ldca(n_pairs, k_log2, ldc_budget, ctypes.byref(lr), ctypes.byref(c), ctypes.byref(psu),
+                            ctypes.byref(star)), "sp_size_ldca")
+    return lr.value, c.value, psu.value, star.value
 
 
 def sp_check_params(p: sp_params) -> int:

@@ -98,3 +98,21 @@ def test_library_limits(sp):
     assert sp.sp_check_params(p) == sp.SP_ERR_PARAM
     p = sp.make_params(n_routers=0)
     assert sp.sp_check_params(p) == sp.SP_ERR_PARAM
+
+
+def test_ldca_sizing_matches_lemma1_and_theorem1(sp):
+    import oracle as O
+    for n, k_log2, budget in [(1 << 26, 10, 1 << 18), (1 << 20, 8, 1 << 12), (1 << 28, 10, 1 << 20), (5000, 6, 64)]:
+        for lr in (1, 3, 4, 8):
+            for c in (4, 10, 16):
+                a, b = sp.sp_psu(n, k_log2, lr, c), O.psu(n, k_log2, lr, 2 ** c)
+                assert abs(a - b) <= 1e-12 * max(b, 1e-300)
+        lr, c, psu, star = sp.sp_size_ldca(n, k_log2, budget)
+        assert abs(star - O.lr_star(n, k_log2, budget)) < 1e-9 * star
+        grid = [(O.psu(n, k_log2, r, 2 ** cc), r, cc) for r in range(1, 9) for cc in range(25)
+                if r * 2 ** cc <= budget and r * 2 ** (cc + k_log2) <= 2 ** 32]
+        best = min(grid)
+        assert (lr, c) == (best[1], best[2]) and abs(psu - best[0]) < 1e-15
+        assert lr * 2 ** c <= budget
+    with pytest.raises(sp.SPError):
+        sp.sp_size_ldca(0, 10, 1 << 16)

@@ -417,3 +417,23 @@ def test_window_pairs_definition():
     assert O.window_pairs(slices, 0, 3).shape == (1, 2)
     w = O.window_pairs(slices, 4, 3)
     assert sorted(set(w[:, 0].tolist())) == [2, 3, 4] and w.shape[0] == 3 + 4 + 5
+
+
+def test_theorem1_is_the_argmin_of_lemma1():
+    """Theorem 1's closed form equals a numeric minimisation (golden-section
+    search) of Lemma 1's Psu over LR with LR * LC = V fixed."""
+    for n, k_log2, v in [(1 << 26, 10, 1 << 18), (1 << 20, 8, 1 << 12), (5e6, 12, 3e5)]:
+        f = lambda lr: O.psu(n, k_log2, lr, v / lr)   # noqa: E731
+        lo, hi = 0.05, 200.0
+        g = (math.sqrt(5) - 1) / 2
+        for _ in range(200):
+            a, b = hi - g * (hi - lo), lo + g * (hi - lo)
+            if f(a) <= f(b):          # ties (the flat Psu = 1 tail) move inward
+                hi = b
+            else:
+                lo = a
+        assert abs((lo + hi) / 2 - O.lr_star(n, k_log2, v)) < 1e-4 * O.lr_star(n, k_log2, v)
+    # at the optimum half the bits of one LDC are set: (1 - 1/k)^(N LR / V) = 1/2
+    n, k_log2, v = 1 << 24, 10, 1 << 16
+    lr = O.lr_star(n, k_log2, v)
+    assert abs((1 - 2.0 ** -k_log2) ** (n * lr / v) - 0.5) < 1e-12
