@@ -148,9 +148,8 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const uint32_t bins = 1u << d.k_log2;
   uint2* raw = reinterpret_cast<uint2*>(smem_raw);                     // [2][kTile]
-  uint32_t* s_sorted = reinterpret_cast<uint32_t*>(raw + 2 * kTile);    // [kTile]
-  uint32_t* s_pos = s_sorted + kTile;                                  // [kTile] list slot or ~0
-  uint32_t* s_count = s_pos + kTile;                                    // [bins] count, then kept
+  uint2* s_entry = raw + 2 * kTile;                                     // [kTile] (hip, list slot or ~0)
+  uint32_t* s_count = reinterpret_cast<uint32_t*>(s_entry + kTile);     // [bins] count, then offset | kept << 14
   uint32_t* s_off = s_count + bins;                                     // [bins] tile offsets
   uint32_t* s_cursor = s_off + bins;                                    // [bins] list fill
   uint32_t* s_dst = s_cursor + bins;                                    // [bins] first free slot
@@ -247,7 +246,7 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
     for (uint32_t b = tid; b < bins; b += kBinThreads) {
       const uint32_t c = s_count[b], have = s_cursor[b];
       const uint32_t keep = have + c <= cap ? c : (cap - have);
-      s_count[b] = keep;
+      s_count[b] = s_off[b] | (keep << 14);      // both <= kTile < 2^14: one lookup below
       s_dst[b] = (b * G + cta) * cap + have;     // list entries < 2^32 (host check)
       s_cursor[b] = have + keep;
     }
@@ -256,16 +255,12 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
     for (int q = 0; q < kPerThread; ++q) {
       if (key[q] != kFull) {
         const uint32_t b = key[q] >> 14, rank = key[q] & 0x3FFFu;
-        // every position of the tile gets its list slot, or ~0 when the list
-        // is full (then the pair is applied in L2 right here)
-        const uint32_t pos = s_off[b] + rank;
-        s_sorted[pos] = hip[q];
-        if (rank < s_count[b]) {
-          s_pos[pos] = s_dst[b] + rank;
-        } else {
-          s_pos[pos] = kFull;
-          ldca_red<LR>(d, ldca, hip[q], b);
-        }
+        // every position of the tile gets (hip, list slot), the slot ~0 when
+        // the list is full (then the pair is applied in L2 right here)
+        const uint32_t ok = s_count[b];
+        const bool kept = rank < (ok >> 14);
+        s_entry[(ok & 0x3FFFu) + rank] = make_uint2(hip[q], kept ? s_dst[b] + rank : kFull);
+        if (!kept) ldca_red<LR>(d, ldca, hip[q], b);
       }
     }
     __syncthreads();
@@ -275,8 +270,8 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
     for (int q = 0; q < kPerThread; ++q) {
       const uint32_t j = (uint32_t)q * kBinThreads + tid;
       if (j < tile_n) {
-        const uint32_t slot = s_pos[j];
-        if (slot != kFull) lists[slot] = s_sorted[j];
+        const uint2 e = s_entry[j];
+        if (e.y != kFull) lists[e.y] = e.x;
       }
     }
     __syncthreads();
