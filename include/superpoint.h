@@ -92,7 +92,7 @@ extern "C" {
  * max_join bounds the LPs that reach the LDCA test in one detect (0 = 1 << 26).
  * scan_mode selects how the LDCA bits of a scan reach memory (results are
  * identical): SP_SCAN_AUTO (0) picks the binned form for updates of at least
- * 2^22 pairs when it applies (k <= 2048, LC >= 32, lr * LC <= 2^20), else the
+ * 2^22 pairs when it applies (k <= 1024, LC >= 32, lr * LC <= 2^20), else the
  * direct form; SP_SCAN_DIRECT (1) sets every bit with an L2 atomic OR;
  * SP_SCAN_BINNED (2) sorts the pairs by LDC bit position, sets the bits of
  * each bit plane with shared-memory atomics and folds the planes into the

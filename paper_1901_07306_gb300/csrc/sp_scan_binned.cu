@@ -27,7 +27,7 @@
 //           a 5-stage butterfly of warp shuffles transposes the 32 x 32 bit
 //           block, giving lane t the 32-bit word of LDC 32 J + t.
 //
-// Applicable when the bins are the LDC's k bit positions (k <= 2048) and one
+// Applicable when the bins are the LDC's k bit positions (k <= 1024) and one
 // plane fits in shared memory as whole words (LC >= 32, LR x LC <= 2^20 bits).
 #include <math.h>
 
@@ -152,7 +152,7 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
   uint32_t* s_count = reinterpret_cast<uint32_t*>(s_entry + kTile);     // [bins] count, then offset | kept << 14
   uint32_t* s_off = s_count + bins;                                     // [bins] tile offsets
   uint32_t* s_cursor = s_off + bins;                                    // [bins] list fill
-  uint32_t* s_dst = s_cursor + bins;                                    // [bins] first free slot
+  uint2* s_meta = reinterpret_cast<uint2*>(s_cursor + bins);            // [bins] (offset | kept << 14, slot)
   __shared__ uint32_t s_warp[32];
   __shared__ __align__(8) uint64_t s_bar[2];
   const uint32_t tid = threadIdx.x;
@@ -246,8 +246,9 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
     for (uint32_t b = tid; b < bins; b += kBinThreads) {
       const uint32_t c = s_count[b], have = s_cursor[b];
       const uint32_t keep = have + c <= cap ? c : (cap - have);
-      s_count[b] = s_off[b] | (keep << 14);      // both <= kTile < 2^14: one lookup below
-      s_dst[b] = (b * G + cta) * cap + have;     // list entries < 2^32 (host check)
+      // offset and kept count (both <= kTile < 2^14) and the first free list
+      // slot (list entries < 2^32, a host check): one 64-bit lookup below
+      s_meta[b] = make_uint2(s_off[b] | (keep << 14), (b * G + cta) * cap + have);
       s_cursor[b] = have + keep;
     }
     __syncthreads();
@@ -257,9 +258,9 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
         const uint32_t b = key[q] >> 14, rank = key[q] & 0x3FFFu;
         // every position of the tile gets (hip, list slot), the slot ~0 when
         // the list is full (then the pair is applied in L2 right here)
-        const uint32_t ok = s_count[b];
-        const bool kept = rank < (ok >> 14);
-        s_entry[(ok & 0x3FFFu) + rank] = make_uint2(hip[q], kept ? s_dst[b] + rank : kFull);
+        const uint2 m = s_meta[b];
+        const bool kept = rank < (m.x >> 14);
+        s_entry[(m.x & 0x3FFFu) + rank] = make_uint2(hip[q], kept ? m.y + rank : kFull);
         if (!kept) ldca_red<LR>(d, ldca, hip[q], b);
       }
     }
@@ -391,8 +392,8 @@ template <int LR>
 cudaError_t bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const BinSrc& src,
                       const BinnedScratch& s, uint32_t cap, bool append, uint32_t rot, cudaStream_t st) {
   const uint32_t bins = 1u << d.k_log2;
-  // raw[2][kTile] pairs, sorted hips, their list slots, 4 counters per bin
-  const size_t bin_smem = (size_t)2 * kTile * 8 + (size_t)kTile * 8 + (size_t)4 * bins * 4;
+  // raw[2][kTile] pairs, (hip, slot) entries, 3 counters and a 64-bit record per bin
+  const size_t bin_smem = (size_t)2 * kTile * 8 + (size_t)kTile * 8 + (size_t)5 * bins * 4;
   cudaError_t e = cudaFuncSetAttribute(k_bin<LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
   if (e != cudaSuccess) return e;
   k_bin<LR><<<s.ctas, kBinThreads, bin_smem, st>>>(d, seav, ldca, src, s.lists, s.counts, cap, s.error,
@@ -415,7 +416,7 @@ cudaError_t apply_round(const DevParams& d, const BinnedScratch& s, uint32_t cap
 
 bool binned_applicable(const DevParams& d) {
   const uint64_t plane_bits = (uint64_t)d.lr << d.lc_log2;
-  return d.k_log2 >= 5 && d.k_log2 <= 11 && d.lc_log2 >= 5 && plane_bits <= (1ull << 20);
+  return d.k_log2 >= 5 && d.k_log2 <= 10 && d.lc_log2 >= 5 && plane_bits <= (1ull << 20);
 }
 
 // List capacity for a round of n_pairs split into `chunks` binning launches:
