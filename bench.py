@@ -481,7 +481,7 @@ def run_serving(args):
         arr = np.cumsum(gaps) - gaps[0]
         rs = [S.Request(router=r.router, pairs=r.pairs, arrival=float(a)) for r, a in zip(reqs, arr)]
         srv = S.SketchServer(n_routers, dict(PROFILE_S, theta=1024, seed=5), budget_bytes=2 << 30,
-                             detect_every=1 << 24, batched=batched)
+                             detect_every=1 << 24, window_slices=args.serve_window_slices, batched=batched)
         try:
             wins = srv.run(rs)
         finally:
@@ -500,7 +500,9 @@ def run_serving(args):
             "dtype": "u32", "data": "synthetic",
             "config": {"workload": f"serving: {n_routers} routers, {len(reqs)} batches of 2^12-2^22 pairs "
                                    "(log-uniform), Poisson arrivals, 2 GiB staging budget, detect every 2^24 "
-                                   "global pairs (OR-merge into a global router), profile S (r=12, LC=2^14)",
+                                   "global pairs (OR-merge into a global router), profile S (r=12, LC=2^14), "
+                                   + (f"sliding window of {args.serve_window_slices} detect periods"
+                                      if args.serve_window_slices > 1 else "discrete windows"),
                        "n_pairs": total, "windows": len(wb)},
             "plain_per_batch": {"value": total / tp, "ms": tp * 1e3},
             "latency_at_half_plain_capacity": {"offered_pairs_per_s": rate, "batched": S.latency_summary(lb),
@@ -529,6 +531,7 @@ def main(argv=None):
     ap.add_argument("--batches-per-router", type=int, default=64)
     ap.add_argument("--slide-total-log2", type=int, default=28)
     ap.add_argument("--requests", type=int, default=400)
+    ap.add_argument("--serve-window-slices", type=int, default=1)
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -1,9 +1,9 @@
 // sp_detect.cu -- end-of-window restore and filter (Sec. 3.2-3.3, Sec. 4.2).
 //
 // k_detect: one warp per SEA (grid-stride over the 2^r SEAs).
-//   1. HSE(i): lanes test 32 SEs of a row at a time for weight >= 3 and a
-//      ballot/popc prefix compacts the hot columns into a per-warp list in
-//      shared memory (Sec. 3.2, "hot SE").
+//   1. HSE(i): lanes test the SEs of a row for weight >= 3 (4 per lane per
+//      32-bit load on rows of 128+ SEs) and a ballot/popc prefix compacts the
+//      hot columns into a per-warp list in shared memory (Sec. 3.2, "hot SE").
 //   2. CIS: lanes split the product HSE(0) x HSE(1); each lane then walks
 //      rows 2 .. SR-1 depth first.  A partial tuple is dropped as soon as two
 //      rows disagree on a shared LP bit (it then matches no LP) or the AND of
@@ -102,13 +102,30 @@ k_detect(DevParams d, const uint8_t* __restrict__ seav, const uint32_t* __restri
     bool empty = false;
     for (uint32_t i = 0; i < d.sr; ++i) {
       const uint32_t sc = 1u << d.ibn[i];
+      const uint8_t* row = sea + d.row_off[i];
       uint32_t n = 0;
-      for (uint32_t c0 = 0; c0 < sc; c0 += 32) {
-        const uint32_t c = c0 + lane;
-        const bool hot = c < sc && __popc((uint32_t)sea[d.row_off[i] + c]) >= 3;
-        const uint32_t bal = __ballot_sync(kFull, hot);
-        if (hot) lists[d.row_off[i] + n + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)c;
-        n += __popc(bal);
+      if (sc >= 128 && ((uintptr_t)row & 3u) == 0) {
+        // rows of 128+ SEs, word aligned: 4 SEs per lane per load; the list
+        // is ordered by (byte of the word, lane), which only changes the order
+        // in which candidates are tried
+        for (uint32_t c0 = 0; c0 < sc; c0 += 128) {
+          const uint32_t w = *reinterpret_cast<const uint32_t*>(row + c0 + 4 * lane);
+#pragma unroll
+          for (uint32_t j = 0; j < 4; ++j) {
+            const bool hot = __popc((w >> (8 * j)) & 0xFFu) >= 3;
+            const uint32_t bal = __ballot_sync(kFull, hot);
+            if (hot) lists[d.row_off[i] + n + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)(c0 + 4 * lane + j);
+            n += __popc(bal);
+          }
+        }
+      } else {
+        for (uint32_t c0 = 0; c0 < sc; c0 += 32) {
+          const uint32_t c = c0 + lane;
+          const bool hot = c < sc && __popc((uint32_t)row[c]) >= 3;
+          const uint32_t bal = __ballot_sync(kFull, hot);
+          if (hot) lists[d.row_off[i] + n + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)c;
+          n += __popc(bal);
+        }
       }
       cnt[i] = n;
       empty |= (n == 0);
