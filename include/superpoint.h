@@ -85,9 +85,11 @@ extern "C" {
  * n_routers sketches (one per simulated watch point) are held by the context.
  * window_slices = 1 is the discrete window of Sec. 3; 2 .. 128 selects the
  * sliding window W(t, k) of Sec. 5 over k = window_slices time slices: every
- * SEAV/LDCA bit becomes a one-byte slice stamp (8x the sketch memory), a bit
- * is active in W(t, k) iff it was set in one of the slices t-k+1 .. t, and
- * sp_slide() advances t (see there).
+ * SEAV/LDCA bit gets a one-byte slice stamp (8x the sketch memory, plus a
+ * second bit sketch: the router's bit sketch collects the current slice, the
+ * other holds the window's bits for detect and export), a bit is active in
+ * W(t, k) iff it was set in one of the slices t-k+1 .. t, and sp_slide()
+ * advances t (see there).
  * max_candidates bounds the detect result buffer (0 = 1 << 20).
  * max_join bounds the LPs that reach the LDCA test in one detect (0 = 1 << 26).
  * scan_mode selects how the LDCA bits of a scan reach memory (results are
@@ -190,7 +192,9 @@ SP_API int sp_reset(sp_ctx* ctx, uint32_t router);
  * row i.  dev_pairs is borrowed until the stream passes the work; it must be
  * 8-byte aligned.  n_pairs = 0 is a no-op.  Bit setting is idempotent and
  * order independent (Sec. 3.4), so updates may be split arbitrarily.
- * In a sliding context the bits are stamped with the current slice.  Async.
+ * In a sliding context the bits go to the router's slice sketch, whose set
+ * bits are stamped with the current slice (and the sketch cleared) before the
+ * slice closes and before a detect, merge or export reads the window.  Async.
  * Errors: SP_ERR_ROUTER, SP_ERR_PARAM (NULL or misaligned pointer), SP_ERR_CUDA. */
 SP_API int sp_update(sp_ctx* ctx, uint32_t router, const uint32_t* dev_pairs, uint64_t n_pairs);
 
@@ -229,7 +233,9 @@ SP_API int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* ro
  * runs, so a CUDA graph that captured this call can be replayed after the
  * caller rewrites the table.  A batch whose router is out of range or whose
  * stream is misaligned is skipped and makes the next sp_results return
- * SP_ERR_ROUTER.  Not valid for sliding contexts (SP_ERR_STATE).  Async. */
+ * SP_ERR_ROUTER.  In a sliding context every router counts as updated (its
+ * slice sketch is committed at the next slide, detect, merge or export).
+ * Async. */
 SP_API int sp_update_batched_device(sp_ctx* ctx, const sp_batch* dev_batches, uint32_t n_batches);
 
 /* Autotuner of the batched launch: times every compiled block shape

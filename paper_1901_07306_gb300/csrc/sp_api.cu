@@ -99,9 +99,13 @@ struct sp_ctx {
   sp::BinnedScratch bs;
   uint32_t** planes = nullptr;              // [n_routers], lazily allocated
   bool* planes_dirty = nullptr;             // bits not yet folded into the LDCA
-  // sliding window (Sec. 5): one stamp byte per bit, per-router slice clock
+  // sliding window (Sec. 5): one stamp byte per bit, per-router slice clock;
+  // the bit sketch of a sliding router holds the current slice's bits until
+  // they are committed to the stamps
   bool sliding = false;
+  bool* slice_dirty = nullptr;              // slice bits not yet committed
   uint8_t* stamps = nullptr;                // n_routers * st_stride bytes
+  uint8_t* window = nullptr;                // n_routers * stride: the window's bits, rebuilt per read
   uint64_t st_seav_pad = 0, st_stride = 0;
   uint64_t* slice = nullptr;                // current slice t of each router
 
@@ -123,8 +127,12 @@ struct sp_ctx {
   uint8_t* st_seav(uint32_t router) const { return stamps + (uint64_t)router * st_stride; }
   uint8_t* st_ldca(uint32_t router) const { return stamps + (uint64_t)router * st_stride + st_seav_pad; }
   uint32_t slice_id(uint32_t router) const { return (uint32_t)(slice[router] % 255u) + 1u; }
+  // SEAV as 32-bit words (the padding past seav_bytes is zero in every region)
+  uint64_t seav_words() const { return (seav_bytes + 3) / 4; }
 
   uint8_t* seav(uint32_t router) const { return sketches + (uint64_t)router * stride; }
+  uint8_t* wseav(uint32_t router) const { return window + (uint64_t)router * stride; }
+  uint32_t* wldca(uint32_t router) const { return reinterpret_cast<uint32_t*>(window + (uint64_t)router * stride + seav_pad); }
   uint32_t* ldca(uint32_t router) const { return reinterpret_cast<uint32_t*>(sketches + (uint64_t)router * stride + seav_pad); }
 };
 
@@ -279,12 +287,14 @@ void sp_destroy(sp_ctx* ctx) {
   }
   free(ctx->planes_dirty);
   free(ctx->slice);
+  free(ctx->slice_dirty);
   for (auto& t : ctx->tables) {
     if (t.host) cudaFreeHost(t.host);
     cudaFree(t.dev);
     if (t.ev) cudaEventDestroy(t.ev);
   }
   cudaFree(ctx->stamps);
+  cudaFree(ctx->window);
   cudaFree(ctx->bs.lists);
   cudaFree(ctx->bs.counts);
   cudaFree(ctx->sketches);
@@ -370,13 +380,15 @@ int sp_create(const sp_params* p, void* cuda_stream, sp_ctx** out) {
     c->planes = static_cast<uint32_t**>(calloc(p->n_routers, sizeof(uint32_t*)));
     c->planes_dirty = static_cast<bool*>(calloc(p->n_routers, sizeof(bool)));
     c->slice = static_cast<uint64_t*>(calloc(p->n_routers, sizeof(uint64_t)));
-    if (!c->planes || !c->planes_dirty || !c->slice) rc = SP_ERR_NOMEM;
+    c->slice_dirty = static_cast<bool*>(calloc(p->n_routers, sizeof(bool)));
+    if (!c->planes || !c->planes_dirty || !c->slice || !c->slice_dirty) rc = SP_ERR_NOMEM;
   }
   if (rc == SP_OK && p->window_slices > 1) {
     c->sliding = true;
     c->st_seav_pad = align_up(c->seav_bytes * 8, kAlign);
     c->st_stride = c->st_seav_pad + align_up(c->ldca_bytes * 8, kAlign);
-    if (cudaMalloc(&c->stamps, c->st_stride * p->n_routers) != cudaSuccess) { cudaGetLastError(); rc = SP_ERR_NOMEM; }
+    if (cudaMalloc(&c->stamps, c->st_stride * p->n_routers) != cudaSuccess ||
+        cudaMalloc(&c->window, c->stride * p->n_routers) != cudaSuccess) { cudaGetLastError(); rc = SP_ERR_NOMEM; }
     else if (sp::launch_zero(c->stamps, c->st_stride * p->n_routers, c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
   }
   if (rc == SP_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
@@ -436,7 +448,7 @@ static int ensure_binned(sp_ctx* ctx, uint32_t router) {
 
 // Whether an update of n pairs takes the binned scan.
 static bool use_binned(const sp_ctx* ctx, uint64_t n_pairs) {
-  if (ctx->sliding || !sp::binned_applicable(ctx->d)) return false;
+  if (!sp::binned_applicable(ctx->d)) return false;
   if (ctx->p.scan_mode == SP_SCAN_BINNED) return true;
   return ctx->p.scan_mode == SP_SCAN_AUTO && n_pairs >= kBinnedMinPairs;
 }
@@ -451,9 +463,7 @@ static sp::BinnedScratch binned_scratch(const sp_ctx* ctx, uint32_t router) {
 
 // One update of one router through the direct or the binned scan.
 static int do_update(sp_ctx* ctx, uint32_t router, const uint32_t* dev_pairs, uint64_t n_pairs) {
-  if (ctx->sliding)
-    return sp::launch_scan_stamp(ctx->d, ctx->st_seav(router), ctx->st_ldca(router), dev_pairs, n_pairs,
-                                 ctx->slice_id(router), ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+  ctx->slice_dirty[router] = true;
   if (use_binned(ctx, n_pairs)) {
     int rc = ensure_binned(ctx, router);
     if (rc != SP_OK) return rc;
@@ -467,18 +477,40 @@ static int do_update(sp_ctx* ctx, uint32_t router, const uint32_t* dev_pairs, ui
                          ctx->scan_grid, ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
 }
 
-// Sliding contexts: the current window's bits into the router's SEAV/LDCA.
-static int materialize(sp_ctx* ctx, uint32_t router) {
+// Sliding contexts: stamps the router's pending slice bits with the current
+// slice id and clears its bit sketch (Sec. 5.2).  The close of a slice and a
+// merge commit first.
+static int commit(sp_ctx* ctx, uint32_t router) {
   if (!ctx->sliding) return SP_OK;
-  return sp::launch_materialize(ctx->st_seav(router), ctx->seav(router), ctx->seav_bytes, ctx->st_ldca(router),
-                                ctx->ldca(router), ctx->ldca_bytes / 4, ctx->slice_id(router),
-                                ctx->p.window_slices, ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+  int rc = fold_router(ctx, router);
+  if (rc != SP_OK || !ctx->slice_dirty[router]) return rc;
+  if (sp::launch_commit(reinterpret_cast<uint32_t*>(ctx->seav(router)), ctx->st_seav(router), ctx->seav_words(),
+                        ctx->ldca(router), ctx->st_ldca(router), ctx->ldca_bytes / 4, ctx->slice_id(router),
+                        ctx->stream) != cudaSuccess)
+    return SP_ERR_CUDA;
+  ctx->slice_dirty[router] = false;
+  return SP_OK;
+}
+
+// Sliding contexts: commit, and the window's bits into the router's window
+// image (what detect and export read).
+static int commit_window(sp_ctx* ctx, uint32_t router) {
+  int rc = fold_router(ctx, router);
+  if (rc != SP_OK) return rc;
+  if (sp::launch_commit_window(reinterpret_cast<uint32_t*>(ctx->seav(router)), ctx->st_seav(router),
+                               ctx->seav_words(), ctx->ldca(router), ctx->st_ldca(router), ctx->ldca_bytes / 4,
+                               reinterpret_cast<uint32_t*>(ctx->wseav(router)), ctx->wldca(router),
+                               ctx->slice_id(router), ctx->p.window_slices, ctx->stream) != cudaSuccess)
+    return SP_ERR_CUDA;
+  ctx->slice_dirty[router] = false;
+  return SP_OK;
 }
 
 int sp_reset(sp_ctx* ctx, uint32_t router) {
   if (!ctx) return SP_ERR_PARAM;
   if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
   ctx->planes_dirty[router] = false;     // pending planes belong to the old window
+  ctx->slice_dirty[router] = false;
   if (ctx->sliding) {
     ctx->slice[router] = 0;
     if (sp::launch_zero(ctx->st_seav(router), ctx->st_stride, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
@@ -514,6 +546,7 @@ int sp_update_host(sp_ctx* ctx, uint32_t router, const uint32_t* host_pairs, uin
   if (rc != SP_OK) return rc;
   const bool binned = use_binned(ctx, n_pairs);
   if (binned && (rc = ensure_binned(ctx, router)) != SP_OK) return rc;
+  ctx->slice_dirty[router] = true;
   const uint32_t bins = 1u << ctx->p.k_log2;
   // Chunks of the host stream go through two device staging buffers: the copy
   // of chunk j + 1 (copy stream) overlaps the scan of chunk j (main stream);
@@ -609,16 +642,11 @@ int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
     if (routers[b] >= ctx->p.n_routers) return SP_ERR_ROUTER;
     if (n_pairs[b] && (!dev_pairs[b] || ((uintptr_t)dev_pairs[b] & 7u))) return SP_ERR_PARAM;
   }
-  if (ctx->sliding) {                       // stamps carry the slice: per batch
-    for (uint32_t b = 0; b < n_batches; ++b) {
-      int rc = sp_update(ctx, routers[b], dev_pairs[b], n_pairs[b]);
-      if (rc != SP_OK) return rc;
-    }
-    return SP_OK;
-  }
   if (capturing(ctx->stream)) return SP_ERR_STATE;
   std::vector<uint64_t> total(ctx->p.n_routers, 0);
   for (uint32_t b = 0; b < n_batches; ++b) total[routers[b]] += n_pairs[b];
+  for (uint32_t r = 0; r < ctx->p.n_routers; ++r)
+    if (total[r]) ctx->slice_dirty[r] = true;
   const uint32_t bins = 1u << ctx->p.k_log2;
   std::vector<sp_batch> rest;
   rest.reserve(n_batches);
@@ -677,16 +705,16 @@ int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
 
 int sp_update_batched_device(sp_ctx* ctx, const sp_batch* dev_batches, uint32_t n_batches) {
   if (!ctx) return SP_ERR_PARAM;
-  if (ctx->sliding) return SP_ERR_STATE;
   if (n_batches == 0) return SP_OK;
   if (!dev_batches || n_batches > 8192) return SP_ERR_PARAM;
+  // the table is read on the device: any router may receive bits
+  for (uint32_t r = 0; r < ctx->p.n_routers; ++r) ctx->slice_dirty[r] = true;
   return launch_table(ctx, dev_batches, n_batches);
 }
 
 int sp_autotune(sp_ctx* ctx, const uint32_t* dev_pairs, uint64_t n_pairs, uint32_t* best_threads,
                 uint32_t* best_blocks) {
   if (!ctx || !dev_pairs || n_pairs == 0 || ((uintptr_t)dev_pairs & 7u)) return SP_ERR_PARAM;
-  if (ctx->sliding) return SP_ERR_STATE;
   const sp_batch one{dev_pairs, n_pairs, 0u, 0u};
   const sp_batch* dev_tab = nullptr;
   int rc = upload_table(ctx, &one, 1, &dev_tab);
@@ -742,10 +770,14 @@ int sp_merge(sp_ctx* ctx, const uint32_t* routers, uint32_t n, uint32_t dst_rout
   if (ctx->sliding) {
     const uint8_t* ssrc[4096];
     uint32_t ms = 0;
-    for (uint32_t i = 0; i < n; ++i) {
+    for (uint32_t i = 0; i < n; ++i)
       if (ctx->slice[routers[i]] != ctx->slice[dst_router]) return SP_ERR_STATE;   // one slice clock
+    int rc = commit(ctx, dst_router);
+    for (uint32_t i = 0; i < n && rc == SP_OK; ++i) {
+      rc = commit(ctx, routers[i]);
       if (routers[i] != dst_router && ms < 4096) ssrc[ms++] = ctx->st_seav(routers[i]);
     }
+    if (rc != SP_OK) return rc;
     return sp::launch_merge_stamp(ctx->st_seav(dst_router), ssrc, ms, ctx->st_stride, ctx->slice_id(dst_router),
                                   ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
   }
@@ -766,12 +798,14 @@ int sp_detect_async(sp_ctx* ctx, uint32_t router, uint32_t threshold) {
   if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
   if (threshold == 0) threshold = ctx->p.theta;
   const uint32_t zt = sp_z_theta(ctx->p.k_log2, threshold);
-  int frc = fold_router(ctx, router);
-  if (frc == SP_OK) frc = materialize(ctx, router);
+  int frc = ctx->sliding ? commit_window(ctx, router) : fold_router(ctx, router);
   if (frc != SP_OK) return frc;
   if (cudaMemsetAsync(ctx->status, 0, sizeof(DetectStatus), ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
-  if (sp::launch_detect(ctx->d, ctx->seav(router), ctx->ldca(router), zt, ctx->keys, ctx->cap,
-                        ctx->p.max_join, ctx->status, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+  // a sliding router is detected on its window image
+  const uint8_t* seav = ctx->sliding ? ctx->wseav(router) : ctx->seav(router);
+  const uint32_t* ldca = ctx->sliding ? ctx->wldca(router) : ctx->ldca(router);
+  if (sp::launch_detect(ctx->d, seav, ldca, zt, ctx->keys, ctx->cap, ctx->p.max_join, ctx->status,
+                        ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
   if (sp::launch_sort_emit(ctx->keys, ctx->cap, ctx->status, ctx->est_table, ctx->p.k_log2,
                            ctx->records, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
   ctx->detect_issued = true;
@@ -837,6 +871,8 @@ int sp_slide(sp_ctx* ctx, uint32_t router) {
   if (!ctx) return SP_ERR_PARAM;
   if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
   if (!ctx->sliding) return sp_reset(ctx, router);   // discrete window: the next period starts empty
+  int rc = commit(ctx, router);                       // slice t's bits carry id(t)
+  if (rc != SP_OK) return rc;
   ctx->slice[router] += 1;
   // sweep segment (t mod M) of the router's counters, M = 255 - k
   const uint64_t M = 255u - ctx->p.window_slices;
@@ -854,9 +890,10 @@ int sp_export(sp_ctx* ctx, uint32_t router, void* host_buf, uint64_t cap, uint64
   *n = total;
   if (!host_buf) return SP_OK;
   if (cap < total) return SP_ERR_TRUNCATED;
-  int frc = fold_router(ctx, router);
-  if (frc == SP_OK) frc = materialize(ctx, router);
+  int frc = ctx->sliding ? commit_window(ctx, router) : fold_router(ctx, router);
   if (frc != SP_OK) return frc;
+  const uint8_t* seav = ctx->sliding ? ctx->wseav(router) : ctx->seav(router);
+  const uint32_t* ldca = ctx->sliding ? ctx->wldca(router) : ctx->ldca(router);
   ImageHeader h;
   memset(&h, 0, sizeof(h));
   memcpy(h.magic, "SPSKETCH", 8);
@@ -871,8 +908,9 @@ int sp_export(sp_ctx* ctx, uint32_t router, void* host_buf, uint64_t cap, uint64
   h.ldca_bytes = ctx->ldca_bytes;
   uint8_t* out = static_cast<uint8_t*>(host_buf);
   memcpy(out, &h, sizeof(h));
-  if (cudaMemcpyAsync(out + sizeof(h), ctx->seav(router), ctx->seav_bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
-      cudaMemcpyAsync(out + sizeof(h) + ctx->seav_bytes, ctx->ldca(router), ctx->ldca_bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+  if (cudaMemcpyAsync(out + sizeof(h), seav, ctx->seav_bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+      cudaMemcpyAsync(out + sizeof(h) + ctx->seav_bytes, ldca, ctx->ldca_bytes, cudaMemcpyDeviceToHost,
+                      ctx->stream) != cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
   const uint64_t sum = fnv1a64(out, total - 8);
   memcpy(out + total - 8, &sum, 8);

@@ -104,12 +104,16 @@ cudaError_t launch_scan_binned(const DevParams& d, uint8_t* seav, uint32_t* ldca
                                uint64_t n_pairs, const BinnedScratch& s, cudaStream_t st);
 // ldca |= transpose(planes)
 cudaError_t launch_fold(const DevParams& d, const uint32_t* planes, uint32_t* ldca, int grid, cudaStream_t st);
-// sliding window (sp_slide.cu)
-cudaError_t launch_scan_stamp(const DevParams& d, uint8_t* st_seav, uint8_t* st_ldca, const uint32_t* pairs,
-                              uint64_t n_pairs, uint32_t id, cudaStream_t s);
+// sliding window (sp_slide.cu); a sketch region is nw 32-bit words, word i
+// owning the 32 stamps [32 i, 32 i + 32) of its stamp region
+// stamps id on the counters of the slice sketch's set bits, then clears the sketch
+cudaError_t launch_commit(uint32_t* seav, uint8_t* st_seav, uint64_t seav_words, uint32_t* ldca,
+                          uint8_t* st_ldca, uint64_t ldca_words, uint32_t id, cudaStream_t s);
+// launch_commit, and the window's bits (active stamps) into wseav / wldca
+cudaError_t launch_commit_window(uint32_t* seav, uint8_t* st_seav, uint64_t seav_words, uint32_t* ldca,
+                                 uint8_t* st_ldca, uint64_t ldca_words, uint32_t* wseav, uint32_t* wldca,
+                                 uint32_t id, uint32_t k, cudaStream_t s);
 cudaError_t launch_clean(uint8_t* stamps, uint64_t lo, uint64_t hi, uint32_t cur, uint32_t k, cudaStream_t s);
-cudaError_t launch_materialize(const uint8_t* st_seav, uint8_t* seav, uint64_t seav_bytes, const uint8_t* st_ldca,
-                               uint32_t* ldca, uint64_t ldca_words, uint32_t cur, uint32_t k, cudaStream_t s);
 cudaError_t launch_merge_stamp(uint8_t* dst, const uint8_t* const* srcs, uint32_t n_src, uint64_t bytes,
                                uint32_t cur, cudaStream_t s);
 cudaError_t launch_merge(uint8_t* dst, const uint8_t* const* srcs, uint32_t n_src,

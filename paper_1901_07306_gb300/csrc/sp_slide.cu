@@ -8,17 +8,23 @@
 // Counter: one byte per bit holding the id of the last slice that set it,
 // id(t) = t mod 255 + 1 (0 = never set).  Its age at slice t is
 // (id(t) - stamp) mod 255, exact as long as the true age is below 255.
-//   k_scan_stamp  the scan of Sec. 3.1-3.3 with "set bit" replaced by
-//                 "store id(t)": every writer of a location in one slice stores
-//                 the same byte, so the update needs no atomics (Sec. 5.2:
-//                 the counters run in parallel).
+//   The scan of Sec. 3.1-3.3 runs unchanged (direct, binned or batched) into
+//   a per-router bit sketch of the current slice: the counters are never the
+//   target of random stores, which on a counter pool larger than L2 would
+//   cost a DRAM read-modify-write per store.
+//   k_commit      stamps id(t) on the counters of every bit set in the slice's
+//                 bit sketch and clears the sketch (one pass over the sketch;
+//                 counters of clear bits keep their stamp).  It runs when the
+//                 slice closes and before a merge reads the counters.
+//   k_commit_window  the same commit fused with one streaming pass over all
+//                 counters that writes the window's bits (active counters) as
+//                 an ordinary SEAV/LDCA: the detect of Sec. 3.2-3.3 and the
+//                 export read that image.
 //   k_clean       at every slide, one of M = 255 - k segments of the counter
 //                 pool is swept and counters of age >= k are reset to 0; each
 //                 counter is swept at most M slices after it expired, so its
 //                 age never reaches 255 and ids never alias (the per-slice
 //                 maintenance of Sec. 5.2, spread over slices).
-//   k_materialize writes the window's bits (active counters) into the
-//                 ordinary SEAV/LDCA, which the detect of Sec. 3.2-3.3 reads.
 //   k_merge_stamp keeps, per counter, the youngest stamp over the routers
 //                 (the OR of Sec. 4.2 for counters of a common slice clock).
 #include "sp_internal.h"
@@ -32,48 +38,6 @@ constexpr int kThreads = 256;
 __device__ __forceinline__ uint32_t age_of(uint32_t stamp, uint32_t cur) {
   return cur >= stamp ? cur - stamp : cur + 255u - stamp;
 }
-
-template <int LR>
-__device__ __forceinline__ void stamp_pair(const DevParams& d, uint8_t* __restrict__ st_seav,
-                                           uint8_t* __restrict__ st_ldca, uint32_t hip, uint32_t oip,
-                                           uint32_t tau_mask, uint8_t id) {
-  const uint32_t h1 = mas(d.ha[0], d.hb[0], oip);
-  if ((h1 & tau_mask) == 0u) {                                 // lsb(H1) >= tau (Sec. 3.1)
-    const uint32_t bit = h1 >> 29;
-    const uint32_t rp = d.r ? (hip & ((1u << d.r) - 1u)) : 0u;
-    const uint32_t lp = (uint32_t)((uint64_t)hip >> d.r);
-    const uint64_t base = (uint64_t)rp * d.sea_bytes;
-    for (uint32_t i = 0; i < d.sr; ++i) {
-      const uint64_t se = base + d.row_off[i] + gather_idx(lp, d.isb[i], d.ibn[i], d.L);
-      st_seav[se * 8u + bit] = id;
-    }
-  }
-  const uint32_t h3 = mas(d.ha[1], d.hb[1], oip) >> (32u - d.k_log2);
-  const uint32_t cshift = 32u - d.lc_log2;
-#pragma unroll
-  for (int i = 0; i < LR; ++i) {
-    const uint32_t col = (uint32_t)((uint64_t)mas(d.ha[2 + i], d.hb[2 + i], hip) >> cshift);
-    const uint64_t ldc = ((uint64_t)i << d.lc_log2) | col;
-    st_ldca[(ldc << d.k_log2) | h3] = id;
-  }
-}
-
-template <int LR>
-__global__ void __launch_bounds__(kThreads)
-k_scan_stamp(DevParams d, uint8_t* __restrict__ st_seav, uint8_t* __restrict__ st_ldca,
-             const uint32_t* __restrict__ pairs, uint64_t n_pairs, uint32_t id) {
-  const uint32_t tau_mask = (1u << d.tau) - 1u;
-  const uint2* p2 = reinterpret_cast<const uint2*>(pairs);
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_pairs;
-       j += (uint64_t)gridDim.x * blockDim.x) {
-    const uint2 v = __ldcs(p2 + j);
-    stamp_pair<LR>(d, st_seav, st_ldca, v.x, v.y, tau_mask, (uint8_t)id);
-  }
-}
-
-// stamps[lo, hi): reset those of age >= k (16 per uint4)
-__global__ void __launch_bounds__(kThreads)
-k_clean(uint4* __restrict__ st, uint64_t lo16, uint64_t hi16, uint32_t cur, uint32_t k);
 
 // Four stamps at once: byte j of the result is 0xFF iff byte j of s is an
 // active stamp (non-zero, age (cur - stamp) mod 255 below k).  Byte-wise
@@ -90,6 +54,7 @@ __device__ __forceinline__ uint32_t active4(uint32_t s, uint32_t cur4, uint32_t 
   return (((active_mask4(s, cur4, k4) & 0x01010101u) * 0x00204081u) >> 21) & 0xFu;
 }
 
+// stamps[lo, hi): reset those of age >= k (16 per uint4)
 __global__ void __launch_bounds__(kThreads)
 k_clean(uint4* __restrict__ st, uint64_t lo16, uint64_t hi16, uint32_t cur, uint32_t k) {
   const uint32_t cur4 = cur * 0x01010101u, k4 = k * 0x01010101u;
@@ -102,23 +67,86 @@ k_clean(uint4* __restrict__ st, uint64_t lo16, uint64_t hi16, uint32_t cur, uint
   }
 }
 
-// SEAV bytes from 8 stamps each; LDCA words from 32 stamps each.
-__global__ void __launch_bounds__(kThreads)
-k_materialize(const uint2* __restrict__ st_seav, uint8_t* __restrict__ seav, uint64_t seav_bytes,
-              const uint4* __restrict__ st_ldca, uint32_t* __restrict__ ldca, uint64_t ldca_words,
-              uint32_t cur, uint32_t k) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t cur4 = cur * 0x01010101u, k4 = k * 0x01010101u;   // k <= 128 < 256
-  for (uint64_t i = t0; i < seav_bytes; i += stride) {
-    const uint2 v = __ldcs(st_seav + i);
-    seav[i] = (uint8_t)(active4(v.x, cur4, k4) | (active4(v.y, cur4, k4) << 4));
+// byte j of the result is 0xFF iff bit j of n is set (n < 16)
+__device__ __forceinline__ uint32_t expand4(uint32_t n) {
+  return ((n * 0x00204081u) & 0x01010101u) * 0xFFu;
+}
+
+// The 32 stamps of one sketch word (stamp j <-> bit j: eight 32-bit lanes of
+// four stamps): id4 is written where the word's bits are set.
+__device__ __forceinline__ void stamp_word(uint32_t bits, uint32_t (&v)[8], uint32_t id4) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const uint32_t m = expand4((bits >> (4 * q)) & 0xFu);
+    v[q] = (v[q] & ~m) | (id4 & m);
   }
-  for (uint64_t i = t0; i < ldca_words; i += stride) {
-    const uint4 a = __ldcs(st_ldca + 2 * i), b = __ldcs(st_ldca + 2 * i + 1);
-    ldca[i] = active4(a.x, cur4, k4) | (active4(a.y, cur4, k4) << 4) | (active4(a.z, cur4, k4) << 8) |
-              (active4(a.w, cur4, k4) << 12) | (active4(b.x, cur4, k4) << 16) | (active4(b.y, cur4, k4) << 20) |
-              (active4(b.z, cur4, k4) << 24) | (active4(b.w, cur4, k4) << 28);
+}
+
+__device__ __forceinline__ void load8(const uint4* st, uint64_t i, uint32_t (&v)[8]) {
+  const uint4 a = st[2 * i], b = st[2 * i + 1];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+__device__ __forceinline__ void store8(uint4* st, uint64_t i, const uint32_t (&v)[8]) {
+  st[2 * i] = make_uint4(v[0], v[1], v[2], v[3]);
+  st[2 * i + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+}
+
+// Commit of one slice: every bit set in the slice's bit sketch stamps its
+// counter with the slice id; counters of unset bits keep their stamp.  The
+// slice sketch is consumed (nonzero words cleared), so the next updates of the
+// router start a fresh slice sketch.  Zero words cost one 4-byte read.
+__global__ void __launch_bounds__(kThreads)
+k_commit(uint32_t* __restrict__ seav, uint4* __restrict__ st_seav, uint64_t seav_words,
+         uint32_t* __restrict__ ldca, uint4* __restrict__ st_ldca, uint64_t ldca_words, uint32_t id) {
+  const uint32_t id4 = id * 0x01010101u;
+  const uint64_t n = seav_words + ldca_words;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x) {
+    const bool in_seav = j < seav_words;
+    uint32_t* sk = in_seav ? seav : ldca;
+    uint4* st = in_seav ? st_seav : st_ldca;
+    const uint64_t i = in_seav ? j : j - seav_words;
+    const uint32_t bits = sk[i];
+    if (bits == 0u) continue;
+    sk[i] = 0u;
+    uint32_t v[8];
+    load8(st, i, v);
+    stamp_word(bits, v, id4);
+    store8(st, i, v);
+  }
+}
+
+// The same commit fused with the read of the window W(t, k): after stamping,
+// bit j of the window word is set iff stamp j is active.  One streaming pass
+// over the stamps (32 bytes per word) feeds the detect and export of a
+// sliding router with an ordinary bit sketch.
+__global__ void __launch_bounds__(kThreads)
+k_commit_window(uint32_t* __restrict__ seav, uint4* __restrict__ st_seav, uint64_t seav_words,
+                uint32_t* __restrict__ ldca, uint4* __restrict__ st_ldca, uint64_t ldca_words,
+                uint32_t* __restrict__ wseav, uint32_t* __restrict__ wldca, uint32_t id, uint32_t k) {
+  const uint32_t id4 = id * 0x01010101u, k4 = k * 0x01010101u;   // k <= 128 < 256
+  const uint64_t n = seav_words + ldca_words;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x) {
+    const bool in_seav = j < seav_words;
+    uint32_t* sk = in_seav ? seav : ldca;
+    uint4* st = in_seav ? st_seav : st_ldca;
+    uint32_t* w = in_seav ? wseav : wldca;
+    const uint64_t i = in_seav ? j : j - seav_words;
+    // the stamps are loaded with the slice word, not after it: one DRAM
+    // round trip per word
+    const uint32_t bits = sk[i];
+    const uint4 a = __ldcs(st + 2 * i), b = __ldcs(st + 2 * i + 1);
+    uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    if (bits != 0u) {
+      sk[i] = 0u;
+      stamp_word(bits, v, id4);
+      store8(st, i, v);
+    }
+    uint32_t out = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) out |= active4(v[q], id4, k4) << (4 * q);
+    w[i] = out;
   }
 }
 
@@ -171,20 +199,19 @@ unsigned grid_for(uint64_t work) {
 
 }  // namespace
 
-cudaError_t launch_scan_stamp(const DevParams& d, uint8_t* st_seav, uint8_t* st_ldca, const uint32_t* pairs,
-                              uint64_t n_pairs, uint32_t id, cudaStream_t s) {
-  if (n_pairs == 0) return cudaSuccess;
-  const unsigned g = grid_for(n_pairs);
-  switch (d.lr) {
-    case 1: k_scan_stamp<1><<<g, kThreads, 0, s>>>(d, st_seav, st_ldca, pairs, n_pairs, id); break;
-    case 2: k_scan_stamp<2><<<g, kThreads, 0, s>>>(d, st_seav, st_ldca, pairs, n_pairs, id); break;
-    case 3: k_scan_stamp<3><<<g, kThreads, 0, s>>>(d, st_seav, st_ldca, pairs, n_pairs, id); break;
-    case 4: k_scan_stamp<4><<<g, kThreads, 0, s>>>(d, st_seav, st_ldca, pairs, n_pairs, id); break;
-    case 5: k_scan_stamp<5><<<g, kThreads, 0, s>>>(d, st_seav, st_ldca, pairs, n_pairs, id); break;
-    case 6: k_scan_stamp<6><<<g, kThreads, 0, s>>>(d, st_seav, st_ldca, pairs, n_pairs, id); break;
-    case 7: k_scan_stamp<7><<<g, kThreads, 0, s>>>(d, st_seav, st_ldca, pairs, n_pairs, id); break;
-    default: k_scan_stamp<8><<<g, kThreads, 0, s>>>(d, st_seav, st_ldca, pairs, n_pairs, id); break;
-  }
+cudaError_t launch_commit(uint32_t* seav, uint8_t* st_seav, uint64_t seav_words, uint32_t* ldca,
+                          uint8_t* st_ldca, uint64_t ldca_words, uint32_t id, cudaStream_t s) {
+  k_commit<<<grid_for(seav_words + ldca_words), kThreads, 0, s>>>(
+      seav, reinterpret_cast<uint4*>(st_seav), seav_words, ldca, reinterpret_cast<uint4*>(st_ldca), ldca_words, id);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_commit_window(uint32_t* seav, uint8_t* st_seav, uint64_t seav_words, uint32_t* ldca,
+                                 uint8_t* st_ldca, uint64_t ldca_words, uint32_t* wseav, uint32_t* wldca,
+                                 uint32_t id, uint32_t k, cudaStream_t s) {
+  k_commit_window<<<grid_for(seav_words + ldca_words), kThreads, 0, s>>>(
+      seav, reinterpret_cast<uint4*>(st_seav), seav_words, ldca, reinterpret_cast<uint4*>(st_ldca), ldca_words,
+      wseav, wldca, id, k);
   return cudaGetLastError();
 }
 
@@ -192,14 +219,6 @@ cudaError_t launch_clean(uint8_t* stamps, uint64_t lo, uint64_t hi, uint32_t cur
   const uint64_t lo16 = lo / 16, hi16 = hi / 16;
   if (hi16 <= lo16) return cudaSuccess;
   k_clean<<<grid_for(hi16 - lo16), kThreads, 0, s>>>(reinterpret_cast<uint4*>(stamps), lo16, hi16, cur, k);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_materialize(const uint8_t* st_seav, uint8_t* seav, uint64_t seav_bytes, const uint8_t* st_ldca,
-                               uint32_t* ldca, uint64_t ldca_words, uint32_t cur, uint32_t k, cudaStream_t s) {
-  const uint64_t work = seav_bytes > ldca_words ? seav_bytes : ldca_words;
-  k_materialize<<<grid_for(work), kThreads, 0, s>>>(reinterpret_cast<const uint2*>(st_seav), seav, seav_bytes,
-                                                   reinterpret_cast<const uint4*>(st_ldca), ldca, ldca_words, cur, k);
   return cudaGetLastError();
 }
 

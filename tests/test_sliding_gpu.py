@@ -144,3 +144,55 @@ def test_sliding_merge_and_reset(sp, torch):
         ctx.update(dev(torch, a[0]), router=1)
         assert same_sketch(ctx, O.Sketch(op).update(a[0]), router=1)
         assert sp.sp_import(ctx.ctx, 1, sp.sp_export(ctx.ctx, 1)) == sp.SP_ERR_STATE
+
+
+@pytest.mark.parametrize("scan_mode", [1, 2])
+def test_every_update_form_mid_slice_reads(sp, torch, scan_mode):
+    """The slice's bits reach the counters however they were scanned (direct
+    or binned; device, host, batched or device-table updates), and a detect
+    or an export in the middle of a slice commits what came so far without
+    losing what comes after it in the same slice."""
+    k = 3
+    kw = dict(TINY, theta=16, seed=21, window_slices=k, n_routers=2, scan_mode=scan_mode)
+    op = oparams(kw)
+    rng = np.random.default_rng(21)
+    parts = [[W.uniform_pairs(int(rng.integers(500, 4000)), seed=1000 + 10 * t + j, n_hosts=150)
+              for j in range(4)] for t in range(7)]
+    keep = []
+    with sp.SuperPoint(**kw) as ctx:
+        for t in range(7):
+            if t:
+                ctx.slide(0)
+                ctx.slide(1)
+            p = parts[t]
+            form = t % 4
+            if form == 0:
+                ctx.update(dev(torch, p[0]))
+                ctx.update_host(np.ascontiguousarray(p[1]))
+            elif form == 1:
+                bufs = [dev(torch, x) for x in p[:2]]
+                sp.sp_update_batched(ctx.ctx, [0, 0], bufs)
+                keep.append(bufs)
+            elif form == 2:
+                bufs = [dev(torch, x) for x in p[:2]]
+                rec = np.zeros(2, sp.BATCH)
+                rec[0] = (bufs[0].data_ptr(), len(p[0]), 0, 0)
+                rec[1] = (bufs[1].data_ptr(), len(p[1]), 0, 0)
+                table = torch.from_numpy(rec.view(np.uint8).copy()).cuda()
+                sp.sp_update_batched_device(ctx.ctx, table, 2)
+                keep.append((bufs, table))
+            else:
+                ctx.update(dev(torch, np.concatenate(p[:2])))
+            # window so far: earlier slices whole, this slice's first two parts
+            so_far = [np.concatenate(x[:4]) for x in parts[:t]] + [np.concatenate(p[:2])]
+            osk = O.sliding_window_sketch(op, so_far, t, k)
+            got, n, _ = ctx.detect()
+            want, n_want, _ = osk.detect()
+            assert n == n_want and np.array_equal(got["ip"], want["ip"]), t
+            assert same_sketch(ctx, osk), t
+            ctx.update(dev(torch, p[2]))
+            ctx.update_host(np.ascontiguousarray(p[3]))
+            whole = [np.concatenate(x[:4]) for x in parts[:t + 1]]
+            assert same_sketch(ctx, O.sliding_window_sketch(op, whole, t, k)), t
+            assert same_sketch(ctx, O.Sketch(op), router=1), t     # router 1 never received pairs
+        torch.cuda.synchronize()
