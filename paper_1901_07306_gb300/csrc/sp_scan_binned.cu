@@ -40,6 +40,7 @@ namespace {
 constexpr int kBinThreads = 1024;
 constexpr int kTile = 8192;                        // pairs per block iteration
 constexpr int kPerThread = kTile / kBinThreads;    // 8
+constexpr int kQueue = 1024;                       // sampled pairs queued per tile
 constexpr int kApplyThreads = 512;
 constexpr int kApplyUnroll = 8;                    // hip loads in flight per lane
 constexpr uint32_t kFull = 0xFFFFFFFFu;
@@ -64,42 +65,6 @@ __device__ __forceinline__ void ldca_red(const DevParams& d, uint32_t* ldca, uin
     const uint32_t col = (uint32_t)((uint64_t)mas(d.ha[2 + i], d.hb[2 + i], hip) >> cshift);
     atomicOr(ldca + (((uint64_t)(((uint32_t)i << d.lc_log2) | col) << wshift) | (h3 >> 5)), 1u << (h3 & 31u));
   }
-}
-
-// Block-wide exclusive scan of n <= 4 * blockDim.x counters in shared memory.
-__device__ void block_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* s_warp) {
-  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  const uint32_t per = (n + blockDim.x - 1) / blockDim.x;     // 1..4
-  uint32_t v[4] = {0, 0, 0, 0}, sum = 0;
-  for (uint32_t j = 0; j < per; ++j) {
-    const uint32_t idx = tid * per + j;
-    v[j] = idx < n ? in[idx] : 0u;
-    sum += v[j];
-  }
-  uint32_t incl = sum;
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(kFull, incl, o);
-    if ((int)lane >= o) incl += y;
-  }
-  if (lane == 31) s_warp[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    const uint32_t nw = blockDim.x >> 5;
-    uint32_t w = lane < nw ? s_warp[lane] : 0u;
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, w, o);
-      if ((int)lane >= o) w += y;
-    }
-    if (lane < nw) s_warp[lane] = w;            // inclusive warp totals
-  }
-  __syncthreads();
-  uint32_t run = (warp ? s_warp[warp - 1] : 0u) + incl - sum;
-  for (uint32_t j = 0; j < per; ++j) {
-    const uint32_t idx = tid * per + j;
-    if (idx < n) out[idx] = run;
-    run += v[j];
-  }
-  __syncthreads();
 }
 
 // ---- TMA 1D bulk copies into shared memory, completed on an mbarrier ------
@@ -139,23 +104,34 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // k_bin: tiles of kTile pairs, tile (cta + i G) in iteration i.  Thread 0
 // prefetches tile i + 1 into the other raw buffer with one TMA bulk copy while
 // the block sorts tile i.  Tiles that are partial, or a stream that is not
-// 16-byte aligned, are read with plain loads instead.
+// 16-byte aligned, are read with plain loads instead.  Per tile:
+//   1. every thread hashes its 8 pairs, counts each pair's bin with a shared
+//      atomic (the count before it is the pair's rank in the bin) and queues
+//      the sampled pairs (Sec. 3.1) for a converged SEAV pass;
+//   2. one thread per bin: exclusive prefix of the counts (warp shuffles plus
+//      one warp over the 32 warp totals), room in the bin's list, the bin's
+//      64-bit record (tile offset | kept << 14, first list slot), count reset;
+//   3. every pair goes to its sorted position with its list slot, and the
+//      queued pairs set their SEAV bits;
+//   4. one thread per sorted position writes the hip: consecutive positions of
+//      a bin land in consecutive list slots.
 template <int LR>
 __global__ void __launch_bounds__(kBinThreads, 1)
 k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
       BinSrc src, uint32_t* __restrict__ lists, uint32_t* __restrict__ counts, uint32_t cap,
       uint32_t* __restrict__ error, bool append, uint32_t rot) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
-  const uint32_t bins = 1u << d.k_log2;
+  const uint32_t bins = 1u << d.k_log2;                                // <= kBinThreads
   uint2* raw = reinterpret_cast<uint2*>(smem_raw);                     // [2][kTile]
   uint2* s_entry = raw + 2 * kTile;                                     // [kTile] (hip, list slot or ~0)
-  uint32_t* s_count = reinterpret_cast<uint32_t*>(s_entry + kTile);     // [bins] count, then offset | kept << 14
-  uint32_t* s_off = s_count + bins;                                     // [bins] tile offsets
-  uint32_t* s_cursor = s_off + bins;                                    // [bins] list fill
-  uint2* s_meta = reinterpret_cast<uint2*>(s_cursor + bins);            // [bins] (offset | kept << 14, slot)
+  uint2* s_meta = s_entry + kTile;                                      // [bins] (offset | kept << 14, slot)
+  uint2* s_queue = s_meta + bins;                                       // [kQueue] sampled (hip, h1)
+  uint32_t* s_count = reinterpret_cast<uint32_t*>(s_queue + kQueue);    // [bins]
+  uint32_t* s_cursor = s_count + bins;                                  // [bins] list fill
   __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_qn;
   __shared__ __align__(8) uint64_t s_bar[2];
-  const uint32_t tid = threadIdx.x;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t G = gridDim.x, cta = blockIdx.x;
   const uint32_t slot = (cta + rot) % G;          // which tiles this block takes
   const uint32_t tau_mask = (1u << d.tau) - 1u;
@@ -169,7 +145,14 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
       acc += (src.n[b] + kTile - 1) / kTile;
       s_tpref[b + 1] = acc;
     }
+    s_qn = 0;
   }
+  // appending continues this block's lists from an earlier chunk of the round
+  if (tid < bins) {
+    s_count[tid] = 0;
+    s_cursor[tid] = append ? counts[(uint64_t)tid * G + cta] : 0u;
+  }
+  if (tid == 0) { mbar_init(&s_bar[0]); mbar_init(&s_bar[1]); }
   __syncthreads();
   const uint64_t n_tiles = s_tpref[src.count];
   auto stream_of = [&](uint64_t tile) {       // the b with s_tpref[b] <= tile < s_tpref[b + 1]
@@ -177,13 +160,6 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
     while (s_tpref[b + 1] <= tile) ++b;
     return b;
   };
-  // appending continues this block's lists from an earlier chunk of the round
-  for (uint32_t b = tid; b < bins; b += kBinThreads) {
-    s_count[b] = 0;
-    s_cursor[b] = append ? counts[(uint64_t)b * G + cta] : 0u;
-  }
-  if (tid == 0) { mbar_init(&s_bar[0]); mbar_init(&s_bar[1]); }
-  __syncthreads();
   // tile of iteration i, and whether it comes through TMA
   auto tile_of = [&](uint64_t i) { return (uint64_t)slot + i * G; };
   auto by_tma = [&](uint64_t tile) {           // a whole tile of a 16-byte aligned stream
@@ -195,7 +171,7 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
     const uint32_t b = stream_of(tile);
     return reinterpret_cast<const uint2*>(src.ptr[b]) + (tile - s_tpref[b]) * kTile;
   };
-  uint32_t uses[2] = {0u, 0u};                  // completed phases of each barrier
+  uint32_t phases = 0u;                          // bit b: parity of barrier b's next phase
   if (tid == 0 && tile_of(0) < n_tiles && by_tma(tile_of(0)))
     tma_load(raw, tile_ptr(tile_of(0)), kTile * 8u, &s_bar[0]);
   for (uint64_t i = 0; tile_of(i) < n_tiles; ++i) {
@@ -205,53 +181,87 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
     const uint64_t next = tile_of(i + 1);
     if (tid == 0 && next < n_tiles && by_tma(next))
       tma_load(raw + (buf ^ 1u) * kTile, tile_ptr(next), kTile * 8u, &s_bar[buf ^ 1u]);
-    const bool full = by_tma(tile);
+    const uint32_t sb = stream_of(tile);
+    const uint64_t base = (tile - s_tpref[sb]) * kTile;                 // within stream sb
+    const bool full = ((uintptr_t)src.ptr[sb] & 15u) == 0 && base + kTile <= src.n[sb];
     if (full) {
-      const bool ok = __syncthreads_and(mbar_wait(&s_bar[buf], uses[buf] & 1u));
-      uses[buf]++;
+      const bool ok = __syncthreads_and(mbar_wait(&s_bar[buf], (phases >> buf) & 1u));
+      phases ^= 1u << buf;
       if (!ok) {
         // give up: flag the error, let this block's copies in flight land
         // (bounded again), publish empty lists and leave
         if (tid == 0) {
           atomicOr(error, 1u);
-          mbar_wait(&s_bar[buf], (uses[buf] - 1u) & 1u);
-          if (next < n_tiles && by_tma(next)) mbar_wait(&s_bar[buf ^ 1u], uses[buf ^ 1u] & 1u);
+          mbar_wait(&s_bar[buf], ((phases >> buf) & 1u) ^ 1u);
+          if (next < n_tiles && by_tma(next)) mbar_wait(&s_bar[buf ^ 1u], (phases >> (buf ^ 1u)) & 1u);
         }
-        for (uint32_t b = tid; b < bins; b += kBinThreads) counts[(uint64_t)b * G + cta] = s_cursor[b];
+        if (tid < bins) counts[(uint64_t)tid * G + cta] = s_cursor[tid];
         return;
       }
     }
-    const uint32_t sb = stream_of(tile);
-    const uint64_t base = (tile - s_tpref[sb]) * kTile;                 // within stream sb
     const uint32_t tile_n = (uint32_t)((src.n[sb] - base) < (uint64_t)kTile ? (src.n[sb] - base) : kTile);
     const uint2* p2 = reinterpret_cast<const uint2*>(src.ptr[sb]);
+    // 1. hash, count, queue the sampled pairs
     uint32_t hip[kPerThread], key[kPerThread];      // key = bin << 14 | rank, ~0 = none
 #pragma unroll
     for (int q = 0; q < kPerThread; ++q) {
       const uint32_t j = (uint32_t)q * kBinThreads + tid;
-      key[q] = kFull;
-      hip[q] = 0;
-      if (j < tile_n) {
-        const uint2 v = full ? raw[buf * kTile + j] : __ldcs(p2 + base + j);
-        const uint32_t h1 = mas(d.ha[0], d.hb[0], v.y);
-        if ((h1 & tau_mask) == 0u) seav_set(d, seav, v.x, h1);
-        const uint32_t h3 = mas(d.ha[1], d.hb[1], v.y) >> h3_shift;
-        hip[q] = v.x;
-        key[q] = (h3 << 14) | atomicAdd(&s_count[h3], 1u);
+      const bool valid = j < tile_n;
+      uint2 v = make_uint2(0u, 0u);
+      if (valid) v = full ? raw[buf * kTile + j] : __ldcs(p2 + base + j);
+      const uint32_t h1 = mas(d.ha[0], d.hb[0], v.y);
+      const bool sampled = valid && (h1 & tau_mask) == 0u;
+      // warp-aggregated push: one shared atomic per warp and round
+      const uint32_t ballot = __ballot_sync(kFull, sampled);
+      if (ballot) {
+        uint32_t first = 0;
+        if (lane == 0) first = atomicAdd(&s_qn, (uint32_t)__popc(ballot));
+        first = __shfl_sync(kFull, first, 0);
+        if (sampled) {
+          const uint32_t at = first + (uint32_t)__popc(ballot & ((1u << lane) - 1u));
+          if (at < (uint32_t)kQueue) s_queue[at] = make_uint2(v.x, h1);
+          else seav_set(d, seav, v.x, h1);          // a queue overflow (small tau) sets the bits here
+        }
       }
+      const uint32_t h3 = mas(d.ha[1], d.hb[1], v.y) >> h3_shift;
+      hip[q] = v.x;
+      key[q] = valid ? ((h3 << 14) | atomicAdd(&s_count[h3], 1u)) : kFull;
     }
     __syncthreads();
-    block_exclusive_scan(s_count, s_off, bins, s_warp);
-    // reserve room in this block's lists; clip at the list capacity
-    for (uint32_t b = tid; b < bins; b += kBinThreads) {
-      const uint32_t c = s_count[b], have = s_cursor[b];
+    // 2. per bin: prefix of the counts, room in the list, record, reset
+    const uint32_t qn = s_qn < (uint32_t)kQueue ? s_qn : (uint32_t)kQueue;
+    const uint32_t c = tid < bins ? s_count[tid] : 0u;
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if ((int)lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = s_warp[lane];                   // 32 warps of 32 threads
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, w, o);
+        if ((int)lane >= o) w += y;
+      }
+      s_warp[lane] = w;                            // inclusive warp totals
+      if (lane == 0) s_qn = 0;                     // every thread has read it
+    }
+    __syncthreads();
+    if (tid < bins) {
+      const uint32_t off = (warp ? s_warp[warp - 1] : 0u) + incl - c;
+      const uint32_t have = s_cursor[tid];
       const uint32_t keep = have + c <= cap ? c : (cap - have);
       // offset and kept count (both <= kTile < 2^14) and the first free list
       // slot (list entries < 2^32, a host check): one 64-bit lookup below
-      s_meta[b] = make_uint2(s_off[b] | (keep << 14), (b * G + cta) * cap + have);
-      s_cursor[b] = have + keep;
+      s_meta[tid] = make_uint2(off | (keep << 14), (tid * G + cta) * cap + have);
+      s_cursor[tid] = have + keep;
+      s_count[tid] = 0;
     }
     __syncthreads();
+    // 3. sorted positions with their list slots; the queued SEAV updates
 #pragma unroll
     for (int q = 0; q < kPerThread; ++q) {
       if (key[q] != kFull) {
@@ -264,8 +274,12 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
         if (!kept) ldca_red<LR>(d, ldca, hip[q], b);
       }
     }
+    for (uint32_t e = tid; e < qn; e += kBinThreads) {
+      const uint2 x = s_queue[e];
+      seav_set(d, seav, x.x, x.y);
+    }
     __syncthreads();
-    // one thread per sorted position: consecutive positions of a bin go to
+    // 4. one thread per sorted position: consecutive positions of a bin go to
     // consecutive list slots
 #pragma unroll
     for (int q = 0; q < kPerThread; ++q) {
@@ -275,11 +289,10 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
         if (e.y != kFull) lists[e.y] = e.x;
       }
     }
-    __syncthreads();
-    for (uint32_t b = tid; b < bins; b += kBinThreads) s_count[b] = 0;
-    __syncthreads();
+    // no barrier here: the next tile writes s_entry (step 3) only after the
+    // barriers of its steps 1 and 2, which every thread reaches after this step
   }
-  for (uint32_t b = tid; b < bins; b += kBinThreads) counts[(uint64_t)b * G + cta] = s_cursor[b];
+  if (tid < bins) counts[(uint64_t)tid * G + cta] = s_cursor[tid];
 }
 
 template <int LR>
@@ -392,8 +405,9 @@ template <int LR>
 cudaError_t bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const BinSrc& src,
                       const BinnedScratch& s, uint32_t cap, bool append, uint32_t rot, cudaStream_t st) {
   const uint32_t bins = 1u << d.k_log2;
-  // raw[2][kTile] pairs, (hip, slot) entries, 3 counters and a 64-bit record per bin
-  const size_t bin_smem = (size_t)2 * kTile * 8 + (size_t)kTile * 8 + (size_t)5 * bins * 4;
+  // raw[2][kTile] pairs, (hip, slot) entries, a 64-bit record and 2 counters
+  // per bin, the sampled-pair queue
+  const size_t bin_smem = (size_t)2 * kTile * 8 + (size_t)kTile * 8 + (size_t)bins * 16 + (size_t)kQueue * 8;
   cudaError_t e = cudaFuncSetAttribute(k_bin<LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
   if (e != cudaSuccess) return e;
   k_bin<LR><<<s.ctas, kBinThreads, bin_smem, st>>>(d, seav, ldca, src, s.lists, s.counts, cap, s.error,
