@@ -23,6 +23,10 @@ constexpr uint64_t kDefaultMaxJoin = 1ull << 26;
 constexpr uint64_t kStagingPairs = 1ull << 22;      // 32 MiB per staging buffer
 constexpr uint64_t kBinnedMinPairs = 1ull << 22;    // auto mode: smaller updates go direct
 constexpr uint64_t kBinnedRoundPairs = 1ull << 26;  // pairs per binning round
+// Host-path binning rounds: each round's plane pass overlaps the next round's
+// copies, so after the last copy only one round of 2^24 pairs is left to apply.
+constexpr uint64_t kHostRoundPairs = 1ull << 24;
+constexpr uint32_t kResultPrefix = 4096;            // records fetched with the status
 constexpr uint64_t kAlign = 256;
 
 uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
@@ -90,6 +94,9 @@ struct sp_ctx {
   uint32_t cap = 0;
   bool detect_issued = false;
   uint32_t last_threshold = 0;
+  // results: status, error word and the first kResultPrefix records land in
+  // one pinned buffer with a single wait
+  uint8_t* result_host = nullptr;
   // host path (Sec. 4.1): two staging buffers and a copy stream
   uint32_t* staging[2] = {nullptr, nullptr};
   cudaStream_t copy_stream = nullptr;
@@ -288,6 +295,7 @@ void sp_destroy(sp_ctx* ctx) {
   free(ctx->planes_dirty);
   free(ctx->slice);
   free(ctx->slice_dirty);
+  if (ctx->result_host) cudaFreeHost(ctx->result_host);
   for (auto& t : ctx->tables) {
     if (t.host) cudaFreeHost(t.host);
     cudaFree(t.dev);
@@ -555,7 +563,8 @@ int sp_update_host(sp_ctx* ctx, uint32_t router, const uint32_t* host_pairs, uin
   uint64_t done = 0;
   uint32_t j = 0;
   while (done < n_pairs) {
-    const uint64_t round_n = binned ? ((n_pairs - done) < ctx->bs.max_pairs ? (n_pairs - done) : ctx->bs.max_pairs)
+    const uint64_t round_cap = ctx->bs.max_pairs < kHostRoundPairs ? ctx->bs.max_pairs : kHostRoundPairs;
+    const uint64_t round_n = binned ? ((n_pairs - done) < round_cap ? (n_pairs - done) : round_cap)
                                     : (n_pairs - done);
     const uint32_t chunks = (uint32_t)((round_n + kStagingPairs - 1) / kStagingPairs);
     const uint32_t cap = binned ? sp::binned_list_cap(round_n, bins, ctx->bs.ctas, chunks) : 0u;
@@ -816,11 +825,27 @@ int sp_detect_async(sp_ctx* ctx, uint32_t router, uint32_t threshold) {
 int sp_results(sp_ctx* ctx, sp_candidate* host_out, uint64_t cap, uint64_t* n_total) {
   if (!ctx || !n_total || (cap && !host_out)) return SP_ERR_PARAM;
   if (!ctx->detect_issued) return SP_ERR_STATE;
+  // status, error word and a prefix of the records come back with one wait
+  constexpr size_t kKerrAt = 64, kRecordsAt = 128;
+  static_assert(sizeof(DetectStatus) <= kKerrAt, "status slot");
+  if (!ctx->result_host &&
+      cudaMallocHost(&ctx->result_host, kRecordsAt + (size_t)kResultPrefix * sizeof(sp_candidate)) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->result_host = nullptr;
+    return SP_ERR_NOMEM;
+  }
+  const uint64_t pre = ctx->cap < kResultPrefix ? ctx->cap : kResultPrefix;
+  if (cudaMemcpyAsync(ctx->result_host, ctx->status, sizeof(DetectStatus), cudaMemcpyDeviceToHost,
+                      ctx->stream) != cudaSuccess ||
+      cudaMemcpyAsync(ctx->result_host + kKerrAt, ctx->kerr, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                      ctx->stream) != cudaSuccess ||
+      (pre && cudaMemcpyAsync(ctx->result_host + kRecordsAt, ctx->records, pre * sizeof(sp_candidate),
+                              cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
   DetectStatus st;
   uint32_t kerr = 0;
-  if (cudaMemcpyAsync(&st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
-      cudaMemcpyAsync(&kerr, ctx->kerr, sizeof(kerr), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
-      cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+  memcpy(&st, ctx->result_host, sizeof(st));
+  memcpy(&kerr, ctx->result_host + kKerrAt, sizeof(kerr));
   if (kerr) {
     // bit 0: a scan kernel gave up a bounded wait (the sketch is incomplete);
     // bit 1: a device batch table named a bad router or stream (batch skipped)
@@ -831,9 +856,11 @@ int sp_results(sp_ctx* ctx, sp_candidate* host_out, uint64_t cap, uint64_t* n_to
   *n_total = st.count;
   const uint64_t avail = st.count < ctx->cap ? st.count : ctx->cap;
   const uint64_t m = avail < cap ? avail : cap;
-  if (m) {
-    if (cudaMemcpyAsync(host_out, ctx->records, m * sizeof(sp_candidate), cudaMemcpyDeviceToHost,
-                        ctx->stream) != cudaSuccess ||
+  const uint64_t staged = m < pre ? m : pre;
+  if (staged) memcpy(host_out, ctx->result_host + kRecordsAt, staged * sizeof(sp_candidate));
+  if (m > staged) {
+    if (cudaMemcpyAsync(host_out + staged, ctx->records + staged, (m - staged) * sizeof(sp_candidate),
+                        cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
         cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
   }
   if (st.overflow) return SP_ERR_CANDIDATE_OVERFLOW;
