@@ -10,9 +10,13 @@
 //      its SEs falls below weight 3 -- AND only clears bits, so the pruning
 //      loses nothing against testing complete tuples (Sec. 3.2, SEU test).
 //   3. A complete tuple fixes every LP bit (Eq. 3, coverage constraint);
-//      ip = LP << r | RP.  Its LDC union (AND over the LR rows, Sec. 3.3) is
-//      read as LR lines of k bits; z0 = k - popc.  The host survives when
-//      z0 <= Z_theta, the integer form of Est >= threshold (Eq. 4).
+//      ip = LP << r | RP goes to a per-warp queue.  When the SEA is done the
+//      warp tests the queued hosts together: the LDC union (AND over the LR
+//      rows, Sec. 3.3) of one host is read as LR lines of k bits spread over
+//      the lanes (one coalesced load per row and lane), z0 = k - popc by a
+//      warp reduction.  The host survives when z0 <= Z_theta, the integer
+//      form of Est >= threshold (Eq. 4).  A full queue falls back to the
+//      same test in one lane.
 //   Survivors are appended as (ip << 32 | z0) keys with one atomic per hit.
 // k_sort_emit: one block sorts the keys (bitonic, in shared memory when they
 //   fit, else in global memory) and writes sp_candidate records with
@@ -25,6 +29,7 @@ namespace {
 
 constexpr int kDetectWarps = 8;
 constexpr int kDetectThreads = kDetectWarps * 32;
+constexpr int kHostQueue = 256;                  // complete tuples queued per warp
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
 struct Found {
@@ -62,32 +67,99 @@ __device__ __forceinline__ uint32_t ldc_zeros(const DevParams& d, const uint32_t
   return (1u << d.k_log2) - ones;
 }
 
-// One complete, consistent tuple: reconstruct the IP and apply the filter.
+__device__ __forceinline__ void keep_host(uint32_t ip, uint32_t z0, uint32_t z_theta, const Found& f) {
+  if (z0 <= z_theta) {
+    const uint32_t slot = atomicAdd(&f.status->count, 1u);
+    if (slot < f.cap) f.keys[slot] = ((uint64_t)ip << 32) | z0;
+    else atomicOr(&f.status->overflow, 1u);
+  }
+}
+
+// One complete, consistent tuple: count it against the join bound and queue
+// its IP for the warp's LDCA test (tested here when the queue is full).
 // Returns false when the detect must stop (a bound was hit).
 __device__ __forceinline__ bool emit_lp(const DevParams& d, const uint32_t* __restrict__ ldca,
                                         uint32_t rp, uint32_t lp, uint32_t z_theta,
-                                        const Found& f, uint32_t& join_local) {
+                                        const Found& f, uint32_t& join_local,
+                                        uint32_t* queue, uint32_t* queue_n) {
   if (++join_local == 64u) {
     const unsigned long long prev = atomicAdd(reinterpret_cast<unsigned long long*>(&f.status->join), 64ull);
     join_local = 0;
     if (prev + 64ull > f.max_join) { atomicOr(&f.status->overflow, 2u); return false; }
   }
   const uint32_t ip = (uint32_t)(((uint64_t)lp << d.r) | rp);
-  const uint32_t z0 = ldc_zeros(d, ldca, ip);
-  if (z0 <= z_theta) {
-    const uint32_t slot = atomicAdd(&f.status->count, 1u);
-    if (slot < f.cap) f.keys[slot] = ((uint64_t)ip << 32) | z0;
-    else atomicOr(&f.status->overflow, 1u);
-  }
+  const uint32_t at = atomicAdd(queue_n, 1u);
+  if (at < (uint32_t)kHostQueue) queue[at] = ip;
+  else keep_host(ip, ldc_zeros(d, ldca, ip), z_theta, f);
   return true;
+}
+
+// The warp's LDCA test of n queued hosts (all lanes call it).  A host's LR
+// lines of wpl words are split over the lanes: with wpl >= 32 each lane
+// takes every 32nd word of each line and two hosts go per pass; with
+// wpl < 32 a pass takes 32 / wpl hosts, one word per lane.
+__device__ void test_queue(const DevParams& d, const uint32_t* __restrict__ ldca, const uint32_t* queue,
+                           uint32_t n, uint32_t z_theta, const Found& f, uint32_t lane) {
+  const uint32_t wpl = 1u << (d.k_log2 - 5u);
+  const uint32_t cshift = 32u - d.lc_log2;
+  const uint32_t k = 1u << d.k_log2;
+  auto line_of = [&](uint32_t ip, uint32_t i) {
+    const uint32_t col = (uint32_t)((uint64_t)mas(d.ha[2 + i], d.hb[2 + i], ip) >> cshift);
+    return ldca + ((uint64_t)((i << d.lc_log2) | col) << (d.k_log2 - 5u));
+  };
+  if (wpl >= 32) {
+    for (uint32_t q = 0; q < n; q += 2) {
+      const bool two = q + 1 < n;
+      const uint32_t ip0 = queue[q], ip1 = two ? queue[q + 1] : ip0;
+      uint32_t ones0 = 0, ones1 = 0;
+      for (uint32_t w = lane; w < wpl; w += 32) {
+        uint32_t u0 = kFull, u1 = kFull;
+        for (uint32_t i = 0; i < d.lr; ++i) {
+          u0 &= line_of(ip0, i)[w];
+          u1 &= line_of(ip1, i)[w];
+        }
+        ones0 += __popc(u0);
+        ones1 += __popc(u1);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ones0 += __shfl_xor_sync(kFull, ones0, o);
+        ones1 += __shfl_xor_sync(kFull, ones1, o);
+      }
+      if (lane == 0) {
+        keep_host(ip0, k - ones0, z_theta, f);
+        if (two) keep_host(ip1, k - ones1, z_theta, f);
+      }
+    }
+  } else {
+    const uint32_t per = 32u / wpl;                 // hosts per pass
+    const uint32_t sub = lane / wpl, w = lane % wpl;
+    for (uint32_t q0 = 0; q0 < n; q0 += per) {
+      const uint32_t q = q0 + sub;
+      uint32_t ones = 0;
+      if (q < n) {
+        const uint32_t ip = queue[q];
+        uint32_t u = kFull;
+        for (uint32_t i = 0; i < d.lr; ++i) u &= line_of(ip, i)[w];
+        ones = __popc(u);
+      }
+      for (uint32_t o = wpl >> 1; o > 0; o >>= 1) ones += __shfl_xor_sync(kFull, ones, o);
+      if (w == 0 && q < n) keep_host(queue[q], k - ones, z_theta, f);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kDetectThreads)
 k_detect(DevParams d, const uint8_t* __restrict__ seav, const uint32_t* __restrict__ ldca,
          uint32_t z_theta, Found f) {
-  extern __shared__ uint16_t s_lists[];
+  extern __shared__ uint32_t s_dyn[];
+  __shared__ uint32_t s_queue_n[kDetectWarps];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-  uint16_t* lists = s_lists + warp * d.sea_bytes;       // row i list at lists + row_off[i]
+  uint32_t* queue = s_dyn + warp * kHostQueue;           // [kDetectWarps][kHostQueue] IPs
+  uint32_t* queue_n = &s_queue_n[warp];
+  uint16_t* lists = reinterpret_cast<uint16_t*>(s_dyn + kDetectWarps * kHostQueue) + warp * d.sea_bytes;
+  if (lane == 0) *queue_n = 0;
+  __syncwarp();
   const uint32_t n_sea = 1u << d.r;
   uint32_t join_local = 0;
   bool stop = false;
@@ -152,7 +224,7 @@ k_detect(DevParams d, const uint8_t* __restrict__ seav, const uint32_t* __restri
           start = 2;
         }
         if (start == d.sr) {
-          if (!emit_lp(d, ldca, rp, kv, z_theta, f, join_local)) stop = true;
+          if (!emit_lp(d, ldca, rp, kv, z_theta, f, join_local, queue, queue_n)) stop = true;
           continue;
         }
         uint32_t pos[8], skm[8], skv[8], sseu[8];
@@ -168,7 +240,7 @@ k_detect(DevParams d, const uint8_t* __restrict__ seav, const uint32_t* __restri
           const uint32_t s2 = sseu[dd] & sea[d.row_off[dd] + c];
           if (((v ^ skv[dd]) & d.cover[dd] & skm[dd]) == 0u && __popc(s2) >= 3) {
             if (dd == (int)d.sr - 1) {
-              if (!emit_lp(d, ldca, rp, skv[dd] | v, z_theta, f, join_local)) stop = true;
+              if (!emit_lp(d, ldca, rp, skv[dd] | v, z_theta, f, join_local, queue, queue_n)) stop = true;
               ++pos[dd];
             } else {
               const int nx = dd + 1;
@@ -181,6 +253,12 @@ k_detect(DevParams d, const uint8_t* __restrict__ seav, const uint32_t* __restri
         }
       }
     }
+    __syncwarp();
+    // 3. the warp's LDCA test of this SEA's complete tuples
+    const uint32_t nq = min(*queue_n, (uint32_t)kHostQueue);
+    if (nq) test_queue(d, ldca, queue, nq, z_theta, f, lane);
+    __syncwarp();
+    if (lane == 0) *queue_n = 0;
     __syncwarp();
     stop = __any_sync(kFull, stop);
   }
@@ -238,7 +316,8 @@ k_sort_emit(uint64_t* keys, uint32_t cap, const DetectStatus* status, const doub
 cudaError_t launch_detect(const DevParams& d, const uint8_t* seav, const uint32_t* ldca,
                           uint32_t z_theta, uint64_t* keys, uint32_t cap, uint64_t max_join,
                           DetectStatus* status, cudaStream_t s) {
-  const size_t smem = (size_t)kDetectWarps * d.sea_bytes * sizeof(uint16_t);
+  const size_t smem = (size_t)kDetectWarps * kHostQueue * sizeof(uint32_t) +
+                      (size_t)kDetectWarps * d.sea_bytes * sizeof(uint16_t);
   cudaError_t e = cudaFuncSetAttribute(k_detect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
