@@ -464,7 +464,6 @@ static bool use_binned(const sp_ctx* ctx, uint64_t n_pairs) {
 static sp::BinnedScratch binned_scratch(const sp_ctx* ctx, uint32_t router) {
   sp::BinnedScratch s = ctx->bs;
   s.planes = ctx->planes[router];
-  s.error = ctx->kerr;
   s.accumulate = ctx->planes_dirty[router];
   return s;
 }

@@ -70,7 +70,6 @@ struct BinnedScratch {
   uint32_t* lists = nullptr;    // [bins][ctas][cap] hips
   uint32_t* counts = nullptr;   // [bins][ctas]
   uint32_t* planes = nullptr;   // [k][LR * LC / 32] plane-major accumulator of one router
-  uint32_t* error = nullptr;    // device word: bit 0 = a bounded wait timed out
   bool accumulate = false;      // planes hold earlier bits (load instead of zero)
   uint32_t ctas = 0;            // persistent binning blocks
   uint64_t max_pairs = 0;       // pairs per binning round the lists are sized for

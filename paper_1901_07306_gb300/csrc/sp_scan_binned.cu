@@ -6,16 +6,14 @@
 // LR = 4, LC = 2^16).  A pair touches exactly one plane, so:
 //
 //  k_bin    (persistent, one 1024-thread block per SM) streams 8K-pair tiles
-//           into shared memory with TMA bulk copies, double buffered (the next
-//           tile lands while this one is sorted; waits on the mbarrier are
-//           bounded and end in an error flag), does the SEAV update of
+//           with 16-byte loads held in registers (the next tile's loads are
+//           issued before the current tile's work), does the SEAV update of
 //           Sec. 3.1-3.2 for sampled pairs (L2 RED, 1 pair in 2^tau), and
-//           counting-sorts each tile by b in shared memory; each bin's run of
-//           hips is appended to the block's private list for that bin, one
-//           thread per sorted position (no global atomics;
-//           lists[b][block][0 .. cap)).  A run that would overflow a list is
-//           applied directly with L2 REDs instead (any input is correct; only
-//           a skewed one is slower).
+//           stages each hip in a shared-memory row of its bin b; a row's whole
+//           8-hip chunks go to the block's private list for that bin with one
+//           32-byte store each (no global atomics; lists[b][block][0 .. cap)).
+//           A row or a list that is full sends its hips to L2 REDs instead
+//           (any input is correct; only a skewed one is slower).
 //  k_apply  (one block per plane) starts the plane in shared memory from
 //           zero (or from the router's pending plane when earlier updates of
 //           the window have not been folded yet), sets bit (i, LH_i(hip)) for
@@ -38,9 +36,13 @@ namespace sp {
 namespace {
 
 constexpr int kBinThreads = 1024;
-constexpr int kTile = 8192;                        // pairs per block iteration
-constexpr int kPerThread = kTile / kBinThreads;    // 8
-constexpr int kQueue = 1024;                       // sampled pairs queued per tile
+constexpr int kVec = 4;                            // 16-byte loads (2 pairs) per thread and tile
+constexpr int kTile = kBinThreads * kVec * 2;      // 8192 pairs per block iteration
+constexpr int kGroup = 8;                          // pairs hashed and staged together
+constexpr int kChunk = 8;                          // hips per list store (32 bytes)
+constexpr int kStage = 28;                         // staged hips per bin (112-byte rows:
+                                                   // 16-byte lane accesses hit all 32 banks)
+constexpr int kQueue = 512;                        // sampled pairs queued per tile
 constexpr int kApplyThreads = 512;
 constexpr int kApplyUnroll = 8;                    // hip loads in flight per lane
 constexpr uint32_t kFull = 0xFFFFFFFFu;
@@ -67,77 +69,50 @@ __device__ __forceinline__ void ldca_red(const DevParams& d, uint32_t* ldca, uin
   }
 }
 
-// ---- TMA 1D bulk copies into shared memory, completed on an mbarrier ------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
+// 256-bit store of 8 hips (a 32-byte aligned list chunk, one full sector).
+__device__ __forceinline__ void st_chunk(uint32_t* dst, uint4 a, uint4 b) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+               :: "l"(dst), "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+               : "memory");
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(bar)) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// One thread: arm the barrier for `bytes` and start the copy (16-byte aligned
-// source and destination, bytes a multiple of 16).
-__device__ __forceinline__ void tma_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-               :: "r"(smem_addr(bar)), "r"(bytes) : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
-}
-
-// Bounded wait for the barrier phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t addr = smem_addr(bar);
-  for (uint32_t it = 0; it < (1u << 20); ++it) {
-    uint32_t done;
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(done) : "r"(addr), "r"(parity) : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-// k_bin: tiles of kTile pairs, tile (cta + i G) in iteration i.  Thread 0
-// prefetches tile i + 1 into the other raw buffer with one TMA bulk copy while
-// the block sorts tile i.  Tiles that are partial, or a stream that is not
-// 16-byte aligned, are read with plain loads instead.  Per tile:
-//   1. every thread hashes its 8 pairs, counts each pair's bin with a shared
-//      atomic (the count before it is the pair's rank in the bin) and queues
-//      the sampled pairs (Sec. 3.1) for a converged SEAV pass;
-//   2. one thread per bin: exclusive prefix of the counts (warp shuffles plus
-//      one warp over the 32 warp totals), room in the bin's list, the bin's
-//      64-bit record (tile offset | kept << 14, first list slot), count reset;
-//   3. every pair goes to its sorted position with its list slot, and the
-//      queued pairs set their SEAV bits;
-//   4. one thread per sorted position writes the hip: consecutive positions of
-//      a bin land in consecutive list slots.
+// k_bin: tiles of kTile pairs, tile (slot + i G) in iteration i.  Each
+// thread holds kVec 16-byte loads (2 pairs each) of a tile in registers and
+// issues the loads of tile i + 1 before it works on tile i, so the copy from
+// HBM overlaps the work.  Tiles that are partial, or a stream that is not
+// 16-byte aligned, are read pair by pair instead.  Every bin owns a staging
+// row of kStage hips in shared memory that persists across tiles (a
+// write-combining buffer for the bin's list).  Per tile:
+//   1. every thread hashes its pairs, queues the sampled pairs (Sec. 3.1) for
+//      a converged SEAV pass, takes a place in its pair's bin row with one
+//      shared atomic and stores the hip there (a row that is full sends the
+//      pair to L2 REDs instead);
+//   2. each thread takes bins tid, tid + kBinThreads, ...: it moves the row's
+//      whole 8-hip chunks to the bin's list with 32-byte stores and keeps the
+//      remainder (< 8 hips) at the front of the row; the queued pairs set
+//      their SEAV bits.
+// At the end the remainders go to the lists with plain stores; an appending
+// launch first takes the tail of a list that is not a whole chunk back into
+// the row, so lists stay dense and chunk stores stay 32-byte aligned.
 template <int LR>
 __global__ void __launch_bounds__(kBinThreads, 1)
 k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
       BinSrc src, uint32_t* __restrict__ lists, uint32_t* __restrict__ counts, uint32_t cap,
-      uint32_t* __restrict__ error, bool append, uint32_t rot) {
+      bool append, uint32_t rot) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
-  const uint32_t bins = 1u << d.k_log2;                                // <= kBinThreads
-  uint2* raw = reinterpret_cast<uint2*>(smem_raw);                     // [2][kTile]
-  uint2* s_entry = raw + 2 * kTile;                                     // [kTile] (hip, list slot or ~0)
-  uint2* s_meta = s_entry + kTile;                                      // [bins] (offset | kept << 14, slot)
-  uint2* s_queue = s_meta + bins;                                       // [kQueue] sampled (hip, h1)
-  uint32_t* s_count = reinterpret_cast<uint32_t*>(s_queue + kQueue);    // [bins]
-  uint32_t* s_cursor = s_count + bins;                                  // [bins] list fill
-  __shared__ uint32_t s_warp[32];
-  __shared__ uint32_t s_qn;
-  __shared__ __align__(8) uint64_t s_bar[2];
-  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const uint32_t bins = 1u << d.k_log2;                                // <= 1024
+  uint32_t* stage = reinterpret_cast<uint32_t*>(smem_raw);             // [bins][kStage]
+  uint2* s_queue = reinterpret_cast<uint2*>(stage + bins * kStage);   // [kQueue] sampled (hip, h1)
+  uint32_t* s_fill = reinterpret_cast<uint32_t*>(s_queue + kQueue);    // [bins] hips in the row
+  uint32_t* s_cursor = s_fill + bins;                                   // [bins] list fill (whole chunks)
+  __shared__ uint32_t s_qn[2];                                          // queue fill, by tile parity
+  __shared__ uint64_t s_tpref[kBinMaxSrc + 1];
+  const uint32_t tid = threadIdx.x;
   const uint32_t G = gridDim.x, cta = blockIdx.x;
   const uint32_t slot = (cta + rot) % G;          // which tiles this block takes
   const uint32_t tau_mask = (1u << d.tau) - 1u;
   const uint32_t h3_shift = 32u - d.k_log2;
   // tiles of the streams, back to back: stream b owns tiles [s_tpref[b], s_tpref[b + 1])
-  __shared__ uint64_t s_tpref[kBinMaxSrc + 1];
   if (tid == 0) {
     uint64_t acc = 0;
     s_tpref[0] = 0;
@@ -145,154 +120,179 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
       acc += (src.n[b] + kTile - 1) / kTile;
       s_tpref[b + 1] = acc;
     }
-    s_qn = 0;
+    s_qn[0] = s_qn[1] = 0;
   }
-  // appending continues this block's lists from an earlier chunk of the round
-  if (tid < bins) {
-    s_count[tid] = 0;
-    s_cursor[tid] = append ? counts[(uint64_t)tid * G + cta] : 0u;
+  auto list_of = [&](uint32_t b) { return lists + ((uint64_t)b * G + cta) * cap; };
+  for (uint32_t b = tid; b < bins; b += kBinThreads) {
+    // an appending launch continues the list: its partial chunk returns to the row
+    const uint32_t have = append ? counts[(uint64_t)b * G + cta] : 0u;
+    const uint32_t tail = have & (kChunk - 1u);
+    for (uint32_t e = 0; e < tail; ++e) stage[b * kStage + e] = list_of(b)[have - tail + e];
+    s_fill[b] = tail;
+    s_cursor[b] = have - tail;
   }
-  if (tid == 0) { mbar_init(&s_bar[0]); mbar_init(&s_bar[1]); }
   __syncthreads();
   const uint64_t n_tiles = s_tpref[src.count];
-  auto stream_of = [&](uint64_t tile) {       // the b with s_tpref[b] <= tile < s_tpref[b + 1]
+  auto tile_of = [&](uint64_t i) { return (uint64_t)slot + i * G; };
+  // a tile: its first pair, its pair count, whether it is read with 16-byte loads
+  struct TileRef { const uint2* p; uint32_t n; bool vec; };
+  auto tile_ref = [&](uint64_t tile) {
     uint32_t b = 0;
     while (s_tpref[b + 1] <= tile) ++b;
-    return b;
+    const uint64_t base = (tile - s_tpref[b]) * kTile;
+    const uint64_t left = src.n[b] - base;
+    TileRef t;
+    t.p = reinterpret_cast<const uint2*>(src.ptr[b]) + base;
+    t.n = left < (uint64_t)kTile ? (uint32_t)left : (uint32_t)kTile;
+    t.vec = ((uintptr_t)src.ptr[b] & 15u) == 0 && t.n == (uint32_t)kTile;
+    return t;
   };
-  // tile of iteration i, and whether it comes through TMA
-  auto tile_of = [&](uint64_t i) { return (uint64_t)slot + i * G; };
-  auto by_tma = [&](uint64_t tile) {           // a whole tile of a 16-byte aligned stream
-    const uint32_t b = stream_of(tile);
-    const uint64_t local = tile - s_tpref[b];
-    return ((uintptr_t)src.ptr[b] & 15u) == 0 && (local + 1) * kTile <= src.n[b];
-  };
-  auto tile_ptr = [&](uint64_t tile) {
-    const uint32_t b = stream_of(tile);
-    return reinterpret_cast<const uint2*>(src.ptr[b]) + (tile - s_tpref[b]) * kTile;
-  };
-  uint32_t phases = 0u;                          // bit b: parity of barrier b's next phase
-  if (tid == 0 && tile_of(0) < n_tiles && by_tma(tile_of(0)))
-    tma_load(raw, tile_ptr(tile_of(0)), kTile * 8u, &s_bar[0]);
-  for (uint64_t i = 0; tile_of(i) < n_tiles; ++i) {
-    const uint64_t tile = tile_of(i);
-    const uint32_t buf = (uint32_t)(i & 1u);
-    // prefetch the next tile into the other buffer (freed at the end of i - 1)
-    const uint64_t next = tile_of(i + 1);
-    if (tid == 0 && next < n_tiles && by_tma(next))
-      tma_load(raw + (buf ^ 1u) * kTile, tile_ptr(next), kTile * 8u, &s_bar[buf ^ 1u]);
-    const uint32_t sb = stream_of(tile);
-    const uint64_t base = (tile - s_tpref[sb]) * kTile;                 // within stream sb
-    const bool full = ((uintptr_t)src.ptr[sb] & 15u) == 0 && base + kTile <= src.n[sb];
-    if (full) {
-      const bool ok = __syncthreads_and(mbar_wait(&s_bar[buf], (phases >> buf) & 1u));
-      phases ^= 1u << buf;
-      if (!ok) {
-        // give up: flag the error, let this block's copies in flight land
-        // (bounded again), publish empty lists and leave
-        if (tid == 0) {
-          atomicOr(error, 1u);
-          mbar_wait(&s_bar[buf], ((phases >> buf) & 1u) ^ 1u);
-          if (next < n_tiles && by_tma(next)) mbar_wait(&s_bar[buf ^ 1u], (phases >> (buf ^ 1u)) & 1u);
-        }
-        if (tid < bins) counts[(uint64_t)tid * G + cta] = s_cursor[tid];
-        return;
-      }
-    }
-    const uint32_t tile_n = (uint32_t)((src.n[sb] - base) < (uint64_t)kTile ? (src.n[sb] - base) : kTile);
-    const uint2* p2 = reinterpret_cast<const uint2*>(src.ptr[sb]);
-    // 1. hash, count, queue the sampled pairs
-    uint32_t hip[kPerThread], key[kPerThread];      // key = bin << 14 | rank, ~0 = none
+  // 16-byte streaming loads of this thread's share of a whole tile; volatile,
+  // so they are issued where they stand (before the work on the previous tile)
+  auto load_tile = [&](uint4 (&r)[kVec], const uint2* p) {
+    const uint4* p4 = reinterpret_cast<const uint4*>(p) + tid;
 #pragma unroll
-    for (int q = 0; q < kPerThread; ++q) {
-      const uint32_t j = (uint32_t)q * kBinThreads + tid;
-      const bool valid = j < tile_n;
-      uint2 v = make_uint2(0u, 0u);
-      if (valid) v = full ? raw[buf * kTile + j] : __ldcs(p2 + base + j);
-      const uint32_t h1 = mas(d.ha[0], d.hb[0], v.y);
-      const bool sampled = valid && (h1 & tau_mask) == 0u;
-      // warp-aggregated push: one shared atomic per warp and round
-      const uint32_t ballot = __ballot_sync(kFull, sampled);
+    for (int u = 0; u < kVec; ++u)
+      asm volatile("ld.global.cs.v4.u32 {%0, %1, %2, %3}, [%4];"
+                   : "=r"(r[u].x), "=r"(r[u].y), "=r"(r[u].z), "=r"(r[u].w) : "l"(p4 + u * kBinThreads));
+  };
+  // step 1 for a group of kGroup pairs (valid: bit q = pair q exists):
+  // hashes, the sampled-pair queue (one warp-aggregated push per pair
+  // position), the row places (independent shared atomics), the staging
+  // stores; a pair whose row is full is marked in the returned mask
+  auto stage_group = [&](const uint32_t (&hip)[kGroup], const uint32_t (&oip)[kGroup], uint32_t valid,
+                         uint32_t par, uint32_t (&bin)[kGroup]) {
+    const uint32_t lane = tid & 31u;
+    uint32_t at[kGroup], over = 0;
+#pragma unroll
+    for (int q = 0; q < kGroup; ++q) {
+      const uint32_t h1 = mas(d.ha[0], d.hb[0], oip[q]);
+      const uint32_t ballot = __ballot_sync(kFull, ((valid >> q) & 1u) && (h1 & tau_mask) == 0u);
       if (ballot) {
         uint32_t first = 0;
-        if (lane == 0) first = atomicAdd(&s_qn, (uint32_t)__popc(ballot));
-        first = __shfl_sync(kFull, first, 0);
-        if (sampled) {
-          const uint32_t at = first + (uint32_t)__popc(ballot & ((1u << lane) - 1u));
-          if (at < (uint32_t)kQueue) s_queue[at] = make_uint2(v.x, h1);
-          else seav_set(d, seav, v.x, h1);          // a queue overflow (small tau) sets the bits here
+        if (lane == 0) first = atomicAdd(&s_qn[par], (uint32_t)__popc(ballot));
+        first = __shfl_sync(kFull, first, 0) + (uint32_t)__popc(ballot & ((1u << lane) - 1u));
+        if (((ballot >> lane) & 1u) && first < (uint32_t)kQueue) s_queue[first] = make_uint2(hip[q], h1);
+        else if ((ballot >> lane) & 1u) over |= 1u << (kGroup + q);   // queue full: SEAV bits directly
+      }
+      bin[q] = mas(d.ha[1], d.hb[1], oip[q]) >> h3_shift;
+    }
+#pragma unroll
+    for (int q = 0; q < kGroup; ++q)
+      at[q] = ((valid >> q) & 1u) ? atomicAdd(&s_fill[bin[q]], 1u) : 0xFFFFu;
+#pragma unroll
+    for (int q = 0; q < kGroup; ++q) {
+      if (at[q] < (uint32_t)kStage) stage[bin[q] * kStage + at[q]] = hip[q];
+      over |= (at[q] >= (uint32_t)kStage && at[q] != 0xFFFFu ? 1u : 0u) << q;
+    }
+    return over;
+  };
+  // the rare leftovers of a group: pairs whose row was full (LDCA bits with
+  // L2 REDs) and sampled pairs the full queue did not take (SEAV bits)
+  auto group_leftovers = [&](const uint32_t (&hip)[kGroup], const uint32_t (&oip)[kGroup],
+                             const uint32_t (&bin)[kGroup], uint32_t over) {
+    if (__any_sync(kFull, over != 0u)) {
+#pragma unroll
+      for (int q = 0; q < kGroup; ++q) {
+        if ((over >> q) & 1u) ldca_red<LR>(d, ldca, hip[q], bin[q]);
+        if ((over >> (kGroup + q)) & 1u) seav_set(d, seav, hip[q], mas(d.ha[0], d.hb[0], oip[q]));
+      }
+    }
+  };
+  // whole chunks of bin b's row (fill f <= kStage) to its list, remainder to the front
+  auto flush_row = [&](uint32_t b, uint32_t f) {
+    uint32_t* row = stage + b * kStage;
+    uint32_t* list = list_of(b);
+    uint32_t cur = s_cursor[b];
+    const uint32_t nch = f / kChunk;
+    for (uint32_t c = 0; c < nch; ++c) {
+      const uint4 x = *reinterpret_cast<const uint4*>(row + c * kChunk);
+      const uint4 y = *reinterpret_cast<const uint4*>(row + c * kChunk + 4);
+      if (cur + kChunk <= cap) {
+        st_chunk(list + cur, x, y);
+        cur += kChunk;
+      } else {                                      // list full: straight to L2
+        const uint32_t h[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+        for (int e = 0; e < 8; ++e) ldca_red<LR>(d, ldca, h[e], b);
+      }
+    }
+    const uint32_t rem = f - nch * kChunk;
+    for (uint32_t e = 0; e < rem; e += 4)           // within the row: nch * 8 + rem <= kStage
+      *reinterpret_cast<uint4*>(row + e) = *reinterpret_cast<const uint4*>(row + nch * kChunk + e);
+    s_fill[b] = rem;
+    s_cursor[b] = cur;
+  };
+  uint4 cur[kVec], nxt[kVec];
+  TileRef tr{nullptr, 0u, false};
+  if (tile_of(0) < n_tiles) {
+    tr = tile_ref(tile_of(0));
+    if (tr.vec) load_tile(cur, tr.p);
+  }
+  for (uint64_t i = 0; tile_of(i) < n_tiles; ++i) {
+    const uint32_t par = (uint32_t)(i & 1u);
+    // the next tile's loads go out before this tile's work
+    TileRef nr{nullptr, 0u, false};
+    if (tile_of(i + 1) < n_tiles) {
+      nr = tile_ref(tile_of(i + 1));
+      if (nr.vec) load_tile(nxt, nr.p);
+    }
+    // 1. hash, queue the sampled pairs, stage the hips in their bins' rows
+    if (tr.vec) {
+#pragma unroll
+      for (int g = 0; g < kVec / (kGroup / 2); ++g) {
+        uint32_t hip[kGroup], oip[kGroup], bin[kGroup];
+#pragma unroll
+        for (int u = 0; u < kGroup / 2; ++u) {
+          const uint4 v = cur[g * (kGroup / 2) + u];
+          hip[2 * u] = v.x; oip[2 * u] = v.y;
+          hip[2 * u + 1] = v.z; oip[2 * u + 1] = v.w;
         }
+        const uint32_t over = stage_group(hip, oip, (1u << kGroup) - 1u, par, bin);
+        group_leftovers(hip, oip, bin, over);
       }
-      const uint32_t h3 = mas(d.ha[1], d.hb[1], v.y) >> h3_shift;
-      hip[q] = v.x;
-      key[q] = valid ? ((h3 << 14) | atomicAdd(&s_count[h3], 1u)) : kFull;
-    }
-    __syncthreads();
-    // 2. per bin: prefix of the counts, room in the list, record, reset
-    const uint32_t qn = s_qn < (uint32_t)kQueue ? s_qn : (uint32_t)kQueue;
-    const uint32_t c = tid < bins ? s_count[tid] : 0u;
-    uint32_t incl = c;
+    } else {
+      for (uint32_t j0 = 0; j0 < (uint32_t)kTile; j0 += kGroup * kBinThreads) {
+        uint32_t hip[kGroup], oip[kGroup], bin[kGroup], valid = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, incl, o);
-      if ((int)lane >= o) incl += y;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t w = s_warp[lane];                   // 32 warps of 32 threads
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, w, o);
-        if ((int)lane >= o) w += y;
-      }
-      s_warp[lane] = w;                            // inclusive warp totals
-      if (lane == 0) s_qn = 0;                     // every thread has read it
-    }
-    __syncthreads();
-    if (tid < bins) {
-      const uint32_t off = (warp ? s_warp[warp - 1] : 0u) + incl - c;
-      const uint32_t have = s_cursor[tid];
-      const uint32_t keep = have + c <= cap ? c : (cap - have);
-      // offset and kept count (both <= kTile < 2^14) and the first free list
-      // slot (list entries < 2^32, a host check): one 64-bit lookup below
-      s_meta[tid] = make_uint2(off | (keep << 14), (tid * G + cta) * cap + have);
-      s_cursor[tid] = have + keep;
-      s_count[tid] = 0;
-    }
-    __syncthreads();
-    // 3. sorted positions with their list slots; the queued SEAV updates
-#pragma unroll
-    for (int q = 0; q < kPerThread; ++q) {
-      if (key[q] != kFull) {
-        const uint32_t b = key[q] >> 14, rank = key[q] & 0x3FFFu;
-        // every position of the tile gets (hip, list slot), the slot ~0 when
-        // the list is full (then the pair is applied in L2 right here)
-        const uint2 m = s_meta[b];
-        const bool kept = rank < (m.x >> 14);
-        s_entry[(m.x & 0x3FFFu) + rank] = make_uint2(hip[q], kept ? m.y + rank : kFull);
-        if (!kept) ldca_red<LR>(d, ldca, hip[q], b);
+        for (int q = 0; q < kGroup; ++q) {
+          const uint32_t j = j0 + (uint32_t)q * kBinThreads + tid;
+          uint2 v = make_uint2(0u, 0u);
+          if (j < tr.n) { v = __ldcs(tr.p + j); valid |= 1u << q; }
+          hip[q] = v.x; oip[q] = v.y;
+        }
+        const uint32_t over = stage_group(hip, oip, valid, par, bin);
+        group_leftovers(hip, oip, bin, over);
       }
     }
-    for (uint32_t e = tid; e < qn; e += kBinThreads) {
+    __syncthreads();
+    // 2. whole chunks to the lists; the queued SEAV updates
+    const uint32_t qn = s_qn[par] < (uint32_t)kQueue ? s_qn[par] : (uint32_t)kQueue;
+    if (tid == 0) s_qn[par ^ 1u] = 0;            // read by every thread before the last barrier
+    for (uint32_t b = tid; b < bins; b += kBinThreads) {
+      const uint32_t f = s_fill[b];
+      if (f >= (uint32_t)kChunk) flush_row(b, f < (uint32_t)kStage ? f : (uint32_t)kStage);
+    }
+    for (uint32_t e = kBinThreads - 1 - tid; e < qn; e += kBinThreads) {
       const uint2 x = s_queue[e];
       seav_set(d, seav, x.x, x.y);
     }
     __syncthreads();
-    // 4. one thread per sorted position: consecutive positions of a bin go to
-    // consecutive list slots
+    tr = nr;
 #pragma unroll
-    for (int q = 0; q < kPerThread; ++q) {
-      const uint32_t j = (uint32_t)q * kBinThreads + tid;
-      if (j < tile_n) {
-        const uint2 e = s_entry[j];
-        if (e.y != kFull) lists[e.y] = e.x;
-      }
-    }
-    // no barrier here: the next tile writes s_entry (step 3) only after the
-    // barriers of its steps 1 and 2, which every thread reaches after this step
+    for (int u = 0; u < kVec; ++u) cur[u] = nxt[u];
   }
-  if (tid < bins) counts[(uint64_t)tid * G + cta] = s_cursor[tid];
+  // remainders (< 8 hips per row) with plain stores
+  for (uint32_t b = tid; b < bins; b += kBinThreads) {
+    const uint32_t f = s_fill[b];
+    uint32_t* list = list_of(b);
+    uint32_t c = s_cursor[b];
+    for (uint32_t e = 0; e < f; ++e) {
+      const uint32_t h = stage[b * kStage + e];
+      if (c < cap) list[c++] = h;
+      else ldca_red<LR>(d, ldca, h, b);
+    }
+    counts[(uint64_t)b * G + cta] = c;
+  }
 }
 
 template <int LR>
@@ -405,13 +405,11 @@ template <int LR>
 cudaError_t bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const BinSrc& src,
                       const BinnedScratch& s, uint32_t cap, bool append, uint32_t rot, cudaStream_t st) {
   const uint32_t bins = 1u << d.k_log2;
-  // raw[2][kTile] pairs, (hip, slot) entries, a 64-bit record and 2 counters
-  // per bin, the sampled-pair queue
-  const size_t bin_smem = (size_t)2 * kTile * 8 + (size_t)kTile * 8 + (size_t)bins * 16 + (size_t)kQueue * 8;
+  // the bins' staging rows, the sampled-pair queue, 2 counters per bin
+  const size_t bin_smem = (size_t)bins * kStage * 4 + (size_t)kQueue * 8 + (size_t)bins * 8;
   cudaError_t e = cudaFuncSetAttribute(k_bin<LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
   if (e != cudaSuccess) return e;
-  k_bin<LR><<<s.ctas, kBinThreads, bin_smem, st>>>(d, seav, ldca, src, s.lists, s.counts, cap, s.error,
-                                                   append, rot);
+  k_bin<LR><<<s.ctas, kBinThreads, bin_smem, st>>>(d, seav, ldca, src, s.lists, s.counts, cap, append, rot);
   return cudaGetLastError();
 }
 
