@@ -38,11 +38,11 @@ namespace {
 constexpr int kBinThreads = 1024;
 constexpr int kVec = 4;                            // 16-byte loads (2 pairs) per thread and tile
 constexpr int kTile = kBinThreads * kVec * 2;      // 8192 pairs per block iteration
-constexpr int kGroup = 8;                          // pairs hashed and staged together
+constexpr int kGroup = 4;                          // pairs hashed and staged together
 constexpr int kChunk = 8;                          // hips per list store (32 bytes)
-constexpr int kStage = 28;                         // staged hips per bin (112-byte rows:
+constexpr int kStage = 44;                         // staged hips per bin (176-byte rows:
                                                    // 16-byte lane accesses hit all 32 banks)
-constexpr int kQueue = 512;                        // sampled pairs queued per tile
+constexpr int kQueue = 512;                        // sampled pairs queued per round of 2 tiles
 constexpr int kApplyThreads = 512;
 constexpr int kApplyUnroll = 8;                    // hip loads in flight per lane
 constexpr uint32_t kFull = 0xFFFFFFFFu;
@@ -136,9 +136,11 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
   auto tile_of = [&](uint64_t i) { return (uint64_t)slot + i * G; };
   // a tile: its first pair, its pair count, whether it is read with 16-byte loads
   struct TileRef { const uint2* p; uint32_t n; bool vec; };
+  uint32_t stream_hint = 0;                      // this block's tiles come in stream order
   auto tile_ref = [&](uint64_t tile) {
-    uint32_t b = 0;
+    uint32_t b = stream_hint;
     while (s_tpref[b + 1] <= tile) ++b;
+    stream_hint = b;
     const uint64_t base = (tile - s_tpref[b]) * kTile;
     const uint64_t left = src.n[b] - base;
     TileRef t;
@@ -222,28 +224,15 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
     s_fill[b] = rem;
     s_cursor[b] = cur;
   };
-  uint4 cur[kVec], nxt[kVec];
-  TileRef tr{nullptr, 0u, false};
-  if (tile_of(0) < n_tiles) {
-    tr = tile_ref(tile_of(0));
-    if (tr.vec) load_tile(cur, tr.p);
-  }
-  for (uint64_t i = 0; tile_of(i) < n_tiles; ++i) {
-    const uint32_t par = (uint32_t)(i & 1u);
-    // the next tile's loads go out before this tile's work
-    TileRef nr{nullptr, 0u, false};
-    if (tile_of(i + 1) < n_tiles) {
-      nr = tile_ref(tile_of(i + 1));
-      if (nr.vec) load_tile(nxt, nr.p);
-    }
-    // 1. hash, queue the sampled pairs, stage the hips in their bins' rows
-    if (tr.vec) {
+  // 1. hash, queue the sampled pairs, stage the hips of one tile in their bins' rows
+  auto stage_tile = [&](const uint4 (&r)[kVec], const TileRef& t, uint32_t par) {
+    if (t.vec) {
 #pragma unroll
       for (int g = 0; g < kVec / (kGroup / 2); ++g) {
         uint32_t hip[kGroup], oip[kGroup], bin[kGroup];
 #pragma unroll
         for (int u = 0; u < kGroup / 2; ++u) {
-          const uint4 v = cur[g * (kGroup / 2) + u];
+          const uint4 v = r[g * (kGroup / 2) + u];
           hip[2 * u] = v.x; oip[2 * u] = v.y;
           hip[2 * u + 1] = v.z; oip[2 * u + 1] = v.w;
         }
@@ -257,29 +246,49 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
         for (int q = 0; q < kGroup; ++q) {
           const uint32_t j = j0 + (uint32_t)q * kBinThreads + tid;
           uint2 v = make_uint2(0u, 0u);
-          if (j < tr.n) { v = __ldcs(tr.p + j); valid |= 1u << q; }
+          if (j < t.n) { v = __ldcs(t.p + j); valid |= 1u << q; }
           hip[q] = v.x; oip[q] = v.y;
         }
         const uint32_t over = stage_group(hip, oip, valid, par, bin);
         group_leftovers(hip, oip, bin, over);
       }
     }
+  };
+  // Rounds of two tiles (i, i + 1) with one flush: the two register buffers
+  // alternate, and each tile's loads go out before the work on the tile
+  // before it.
+  uint4 ra[kVec], rb[kVec];
+  TileRef ta{nullptr, 0u, false}, tb{nullptr, 0u, false};
+  if (tile_of(0) < n_tiles) {
+    ta = tile_ref(tile_of(0));
+    if (ta.vec) load_tile(ra, ta.p);
+  }
+  uint32_t par = 0;
+  for (uint64_t i = 0; tile_of(i) < n_tiles; i += 2, par ^= 1u) {
+    const bool has_b = tile_of(i + 1) < n_tiles;
+    if (has_b) {
+      tb = tile_ref(tile_of(i + 1));
+      if (tb.vec) load_tile(rb, tb.p);
+    }
+    stage_tile(ra, ta, par);
+    if (tile_of(i + 2) < n_tiles) {
+      ta = tile_ref(tile_of(i + 2));
+      if (ta.vec) load_tile(ra, ta.p);
+    }
+    if (has_b) stage_tile(rb, tb, par);
     __syncthreads();
-    // 2. whole chunks to the lists; the queued SEAV updates
+    // 2. whole chunks to the lists; the queued SEAV updates, spread over the warps
     const uint32_t qn = s_qn[par] < (uint32_t)kQueue ? s_qn[par] : (uint32_t)kQueue;
     if (tid == 0) s_qn[par ^ 1u] = 0;            // read by every thread before the last barrier
     for (uint32_t b = tid; b < bins; b += kBinThreads) {
       const uint32_t f = s_fill[b];
       if (f >= (uint32_t)kChunk) flush_row(b, f < (uint32_t)kStage ? f : (uint32_t)kStage);
     }
-    for (uint32_t e = kBinThreads - 1 - tid; e < qn; e += kBinThreads) {
+    for (uint32_t e = (tid & 31u) * 32u + (tid >> 5); e < qn; e += kBinThreads) {
       const uint2 x = s_queue[e];
       seav_set(d, seav, x.x, x.y);
     }
     __syncthreads();
-    tr = nr;
-#pragma unroll
-    for (int u = 0; u < kVec; ++u) cur[u] = nxt[u];
   }
   // remainders (< 8 hips per row) with plain stores
   for (uint32_t b = tid; b < bins; b += kBinThreads) {
@@ -304,32 +313,34 @@ k_apply(DevParams d, const uint32_t* __restrict__ lists, const uint32_t* __restr
   const uint32_t words = ((uint32_t)LR << d.lc_log2) >> 5;       // plane words
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t nwarps = kApplyThreads / 32;
+  // LH_i(hip) = h >> cshift (5 <= lc_log2 <= 20): LDC h >> cshift of row i is
+  // bit (h >> cshift) & 31 of plane word (i << (lc_log2 - 5)) + (h >> (cshift + 5))
   const uint32_t cshift = 32u - d.lc_log2;
+  const uint32_t row_words_log2 = d.lc_log2 - 5u;
   uint32_t* dst = planes + (uint64_t)b * words;
   for (uint32_t w = tid; w < words; w += kApplyThreads) s_plane[w] = accumulate ? dst[w] : 0u;
   __syncthreads();
+  auto set_bits = [&](uint32_t hip) {
+#pragma unroll
+    for (int r = 0; r < LR; ++r) {
+      const uint32_t h = mas(d.ha[2 + r], d.hb[2 + r], hip);
+      // the clamping funnel shift gives 0 for the shift of 32 at lc_log2 = 5
+      atomicOr(&s_plane[((uint32_t)r << row_words_log2) + __funnelshift_rc(h, 0u, cshift + 5u)],
+               1u << ((h >> cshift) & 31u));
+    }
+  };
   for (uint32_t c = warp; c < G; c += nwarps) {
     const uint32_t n = counts[(uint64_t)b * G + c];
-    const uint32_t* src = lists + ((uint64_t)b * G + c) * cap;
-    for (uint32_t i0 = 0; i0 < n; i0 += 32 * kApplyUnroll) {
+    const uint32_t* src = lists + ((uint64_t)b * G + c) * cap + lane;
+    uint32_t i0 = 0;
+    for (; i0 + 32 * kApplyUnroll <= n; i0 += 32 * kApplyUnroll) {     // whole rounds: no bounds checks
       uint32_t hip[kApplyUnroll];
 #pragma unroll
-      for (int u = 0; u < kApplyUnroll; ++u) {          // all loads first: kApplyUnroll in flight
-        const uint32_t i = i0 + (uint32_t)u * 32 + lane;
-        hip[u] = i < n ? __ldcs(src + i) : 0u;
-      }
+      for (int u = 0; u < kApplyUnroll; ++u) hip[u] = __ldcs(src + i0 + u * 32);   // all loads in flight
 #pragma unroll
-      for (int u = 0; u < kApplyUnroll; ++u) {
-        if (i0 + (uint32_t)u * 32 + lane < n) {
-#pragma unroll
-          for (int r = 0; r < LR; ++r) {
-            const uint32_t col = (uint32_t)((uint64_t)mas(d.ha[2 + r], d.hb[2 + r], hip[u]) >> cshift);
-            const uint32_t bit = ((uint32_t)r << d.lc_log2) | col;
-            atomicOr(&s_plane[bit >> 5], 1u << (bit & 31u));
-          }
-        }
-      }
+      for (int u = 0; u < kApplyUnroll; ++u) set_bits(hip[u]);
     }
+    for (uint32_t i = i0 + lane; i < n; i += 32) set_bits(__ldcs(src - lane + i));
   }
   __syncthreads();
   for (uint32_t w = tid; w < words; w += kApplyThreads) dst[w] = s_plane[w];
