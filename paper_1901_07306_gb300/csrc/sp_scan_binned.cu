@@ -314,7 +314,7 @@ k_apply(DevParams d, const uint32_t* __restrict__ lists, const uint32_t* __restr
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t nwarps = kApplyThreads / 32;
   // LH_i(hip) = h >> cshift (5 <= lc_log2 <= 20): LDC h >> cshift of row i is
-  // bit (h >> cshift) & 31 of plane word (i << (lc_log2 - 5)) + (h >> (cshift + 5))
+  // bit (h >> cshift) mod 32 of plane word (i << (lc_log2 - 5)) + (h >> (cshift + 5))
   const uint32_t cshift = 32u - d.lc_log2;
   const uint32_t row_words_log2 = d.lc_log2 - 5u;
   uint32_t* dst = planes + (uint64_t)b * words;
@@ -324,9 +324,10 @@ k_apply(DevParams d, const uint32_t* __restrict__ lists, const uint32_t* __restr
 #pragma unroll
     for (int r = 0; r < LR; ++r) {
       const uint32_t h = mas(d.ha[2 + r], d.hb[2 + r], hip);
-      // the clamping funnel shift gives 0 for the shift of 32 at lc_log2 = 5
+      // the clamping funnel shift gives 0 for the shift of 32 at lc_log2 = 5;
+      // the wrapping one takes the bit position mod 32
       atomicOr(&s_plane[((uint32_t)r << row_words_log2) + __funnelshift_rc(h, 0u, cshift + 5u)],
-               1u << ((h >> cshift) & 31u));
+               __funnelshift_l(0u, 1u, h >> cshift));
     }
   };
   for (uint32_t c = warp; c < G; c += nwarps) {
