@@ -448,7 +448,10 @@ static int ensure_binned(sp_ctx* ctx, uint32_t router) {
     }
   }
   if (!ctx->planes[router]) {
-    if (cudaMalloc(&ctx->planes[router], ctx->ldca_bytes) != cudaSuccess) { cudaGetLastError(); return SP_ERR_NOMEM; }
+    if (cudaMalloc(&ctx->planes[router], sp::binned_planes_bytes(ctx->d)) != cudaSuccess) {
+      cudaGetLastError();
+      return SP_ERR_NOMEM;
+    }
     ctx->planes_dirty[router] = false;
   }
   return SP_OK;

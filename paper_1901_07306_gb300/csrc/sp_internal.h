@@ -69,7 +69,7 @@ struct BinSrc {
 struct BinnedScratch {
   uint32_t* lists = nullptr;    // [bins][ctas][cap] hips
   uint32_t* counts = nullptr;   // [bins][ctas]
-  uint32_t* planes = nullptr;   // [k][LR * LC / 32] plane-major accumulator of one router
+  uint32_t* planes = nullptr;   // plane accumulator of one router, [ceil(W / 8)][k][8] words, W = LR * LC / 32
   bool accumulate = false;      // planes hold earlier bits (load instead of zero)
   uint32_t ctas = 0;            // persistent binning blocks
   uint64_t max_pairs = 0;       // pairs per binning round the lists are sized for
@@ -89,6 +89,8 @@ int multi_max_grid(int threads);
 bool binned_applicable(const DevParams& d);
 uint32_t binned_list_cap(uint64_t n_pairs, uint32_t bins, uint32_t ctas, uint32_t chunks);
 uint32_t binned_tile_pairs();
+// bytes of one router's plane accumulator ([ceil(W / 8)][k][8] words)
+uint64_t binned_planes_bytes(const DevParams& d);
 // one binning launch over pairs[0, n) into the lists (append: continue them)
 cudaError_t binned_bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const BinSrc& src,
                              const BinnedScratch& s, uint32_t cap, bool append, uint32_t rot, cudaStream_t st);

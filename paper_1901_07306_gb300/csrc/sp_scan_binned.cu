@@ -20,7 +20,7 @@
 //           every listed hip and row i with shared atomic OR, and stores the
 //           plane back (the block owns it).
 //  k_fold   (before the next detect, merge or export of the router) ORs the
-//           plane-major accumulator into the LDCA's logical layout
+//           plane accumulator into the LDCA's logical layout
 //           [LR][LC][k / 32]: a warp loads word J of 32 consecutive planes and
 //           a 5-stage butterfly of warp shuffles transposes the 32 x 32 bit
 //           block, giving lane t the 32-bit word of LDC 32 J + t.
@@ -317,8 +317,12 @@ k_apply(DevParams d, const uint32_t* __restrict__ lists, const uint32_t* __restr
   // bit (h >> cshift) mod 32 of plane word (i << (lc_log2 - 5)) + (h >> (cshift + 5))
   const uint32_t cshift = 32u - d.lc_log2;
   const uint32_t row_words_log2 = d.lc_log2 - 5u;
-  uint32_t* dst = planes + (uint64_t)b * words;
-  for (uint32_t w = tid; w < words; w += kApplyThreads) s_plane[w] = accumulate ? dst[w] : 0u;
+  // accumulator layout [ceil(words / 8)][k][8]: word w of plane b at
+  // (w / 8) k 8 + 8 b + w mod 8, so that a 32-byte chunk holds 8 words of one plane
+  const uint64_t chunk_stride = (uint64_t)(1u << d.k_log2) * 8u;
+  uint32_t* dst = planes + (uint64_t)b * 8u;
+  auto at_word = [&](uint32_t w) { return dst + (uint64_t)(w >> 3) * chunk_stride + (w & 7u); };
+  for (uint32_t w = tid; w < words; w += kApplyThreads) s_plane[w] = accumulate ? *at_word(w) : 0u;
   __syncthreads();
   auto set_bits = [&](uint32_t hip) {
 #pragma unroll
@@ -344,7 +348,7 @@ k_apply(DevParams d, const uint32_t* __restrict__ lists, const uint32_t* __restr
     for (uint32_t i = i0 + lane; i < n; i += 32) set_bits(__ldcs(src - lane + i));
   }
   __syncthreads();
-  for (uint32_t w = tid; w < words; w += kApplyThreads) dst[w] = s_plane[w];
+  for (uint32_t w = tid; w < words; w += kApplyThreads) *at_word(w) = s_plane[w];
 }
 
 // 32 x 32 bit transpose across a warp: lane l holds row l (bit j = column j);
@@ -360,17 +364,18 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, uint32_t lane) {
   return x;
 }
 
-// planes: [k][W] words (W = LR * LC / 32); ldca: [LR * LC][k / 32] words.
-// A warp task is 8 consecutive plane words J0 .. J0 + 7 (one 32-byte sector
-// of each plane it reads) times 4 consecutive LDC words: it transposes
-// 32 planes x 32 LDCs per word and ORs the result into the lanes' LDC lines.
+// planes: [ceil(W / 8)][k][8] words (W = LR * LC / 32 words per plane, 8-word
+// chunks of the k planes side by side); ldca: [LR * LC][k / 32] words.
+// A warp task is 8 consecutive plane words J0 .. J0 + 7 (one 32-byte chunk of
+// each plane it reads; 32 planes' chunks are 1 KiB of contiguous memory)
+// times 4 consecutive LDC words: it transposes 32 planes x 32 LDCs per word
+// and ORs the result into the lanes' LDC lines.
 __global__ void __launch_bounds__(256)
 k_fold(const uint32_t* __restrict__ planes, uint32_t* __restrict__ ldca, uint32_t W, uint32_t k_log2) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t wpl = 1u << (k_log2 - 5u);                       // words per LDC
   const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  const bool vec = (W & 7u) == 0 && wpl >= 4;
   const uint64_t n_groups = (W + 7) / 8;
   const uint32_t n_q = (wpl + 3) / 4;                              // groups of 4 LDC words
   for (uint64_t t = gwarp; t < n_groups * n_q; t += nwarp) {
@@ -383,16 +388,12 @@ k_fold(const uint32_t* __restrict__ planes, uint32_t* __restrict__ ldca, uint32_
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const uint32_t q = q0 + u;
-        const uint32_t* row = planes + (uint64_t)(q * 32u + lane) * W + J0;
-        if (vec) {
-          const uint4 a = *reinterpret_cast<const uint4*>(row);
-          const uint4 c = *reinterpret_cast<const uint4*>(row + 4);
-          x[u][0] = a.x; x[u][1] = a.y; x[u][2] = a.z; x[u][3] = a.w;
-          x[u][4] = c.x; x[u][5] = c.y; x[u][6] = c.z; x[u][7] = c.w;
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) x[u][j] = (q < wpl && (uint32_t)j < nj) ? row[j] : 0u;
-        }
+        const uint32_t keep = q < wpl ? kFull : 0u;     // planes past k (k < 128 only) read as zero
+        const uint4* chunk = reinterpret_cast<const uint4*>(planes + g * ((uint64_t)wpl * 256u) +
+                                                            (uint64_t)((q < wpl ? q : 0u) * 32u + lane) * 8u);
+        const uint4 a = chunk[0], c = chunk[1];
+        x[u][0] = a.x & keep; x[u][1] = a.y & keep; x[u][2] = a.z & keep; x[u][3] = a.w & keep;
+        x[u][4] = c.x & keep; x[u][5] = c.y & keep; x[u][6] = c.z & keep; x[u][7] = c.w & keep;
       }
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
@@ -511,6 +512,11 @@ cudaError_t binned_apply_round(const DevParams& d, const BinnedScratch& s, uint3
 }
 
 uint32_t binned_tile_pairs() { return (uint32_t)kTile; }
+
+uint64_t binned_planes_bytes(const DevParams& d) {
+  const uint64_t words = ((uint64_t)d.lr << d.lc_log2) >> 5;          // per plane
+  return ((words + 7) / 8) * 8 * ((uint64_t)1 << d.k_log2) * sizeof(uint32_t);
+}
 
 cudaError_t launch_scan_binned(const DevParams& d, uint8_t* seav, uint32_t* ldca, const uint32_t* pairs,
                                uint64_t n_pairs, const BinnedScratch& s, cudaStream_t st) {
