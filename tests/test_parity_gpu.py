@@ -84,6 +84,20 @@ def test_scan_parity_sizes_and_alignment(sp, torch, n, offset, mode):
         assert_same_sketch(ctx, O.Sketch(oracle_params(kw)).update(pairs))
 
 
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n", [4099, 200003])
+def test_scan_parity_smallest_binned_planes(sp, torch, n, mode):
+    """The smallest sketch the binned scan takes: k = 32 bit planes of
+    LR x LC = 2 x 32 bits (the plane word index is a shift by 32, and one
+    LDC is a single word), bit-exact in both scan forms."""
+    kw = dict(r=12, isb=(0, 7, 14), ibn=(8, 8, 8), k_log2=5, lr=2, lc_log2=5, theta=16, seed=19, scan_mode=mode)
+    pairs = W.uniform_pairs(n, seed=n + 11, n_hosts=max(1, n // 20))
+    with sp.SuperPoint(**kw) as ctx:
+        ctx.update(dev(torch, pairs))
+        torch.cuda.synchronize()
+        assert_same_sketch(ctx, O.Sketch(oracle_params(kw)).update(pairs))
+
+
 # (profile, workload) pairs sized so that no SEA is overloaded: the oracle
 # enumerates the full cartesian product of hot SEs, as the paper states it
 PROFILES = [
