@@ -414,6 +414,47 @@ k_fold(const uint32_t* __restrict__ planes, uint32_t* __restrict__ ldca, uint32_
   }
 }
 
+// k_fold8 (k >= 256): a warp task is 8 plane words J0 .. J0 + 7 times 8
+// consecutive LDC words q0 .. q0 + 7, so each lane ORs one whole 32-byte
+// sector into each of its 8 LDC lines; the 8 chunks of 8 planes' words are
+// loaded up front (16 loads in flight per lane).
+__global__ void __launch_bounds__(256)
+k_fold8(const uint32_t* __restrict__ planes, uint32_t* __restrict__ ldca, uint32_t W, uint32_t k_log2) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t wpl = 1u << (k_log2 - 5u);                       // words per LDC, >= 8
+  const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const uint64_t n_groups = (W + 7) / 8;
+  const uint32_t n_q = wpl / 8;                                    // groups of 8 LDC words
+  for (uint64_t t = gwarp; t < n_groups * n_q; t += nwarp) {
+    const uint64_t g = t / n_q;
+    const uint32_t J0 = (uint32_t)(g * 8);
+    const uint32_t nj = (W - J0) < 8u ? (W - J0) : 8u;
+    const uint32_t q0 = (uint32_t)(t % n_q) * 8u;
+    uint32_t x[8][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const uint4* chunk = reinterpret_cast<const uint4*>(planes + g * ((uint64_t)wpl * 256u) +
+                                                          (uint64_t)((q0 + u) * 32u + lane) * 8u);
+      const uint4 a = chunk[0], c = chunk[1];
+      x[u][0] = a.x; x[u][1] = a.y; x[u][2] = a.z; x[u][3] = a.w;
+      x[u][4] = c.x; x[u][5] = c.y; x[u][6] = c.z; x[u][7] = c.w;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if ((uint32_t)j >= nj) break;
+      uint4* line = reinterpret_cast<uint4*>(ldca + ((uint64_t)(J0 + j) * 32u + lane) * wpl + q0);
+      uint4 o0 = line[0], o1 = line[1];
+      o0.x |= transpose32(x[0][j], lane); o0.y |= transpose32(x[1][j], lane);
+      o0.z |= transpose32(x[2][j], lane); o0.w |= transpose32(x[3][j], lane);
+      o1.x |= transpose32(x[4][j], lane); o1.y |= transpose32(x[5][j], lane);
+      o1.z |= transpose32(x[6][j], lane); o1.w |= transpose32(x[7][j], lane);
+      line[0] = o0;
+      line[1] = o1;
+    }
+  }
+}
+
 template <int LR>
 cudaError_t bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const BinSrc& src,
                       const BinnedScratch& s, uint32_t cap, bool append, uint32_t rot, cudaStream_t st) {
@@ -470,7 +511,8 @@ int binned_fold_grid() {
 
 cudaError_t launch_fold(const DevParams& d, const uint32_t* planes, uint32_t* ldca, int grid, cudaStream_t st) {
   const uint32_t words = (uint32_t)(((uint64_t)d.lr << d.lc_log2) >> 5);
-  k_fold<<<grid, 256, 0, st>>>(planes, ldca, words, d.k_log2);
+  if (d.k_log2 >= 8) k_fold8<<<grid, 256, 0, st>>>(planes, ldca, words, d.k_log2);
+  else k_fold<<<grid, 256, 0, st>>>(planes, ldca, words, d.k_log2);
   return cudaGetLastError();
 }
 
