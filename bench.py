@@ -78,6 +78,18 @@ def scan_traffic_from_profile(n_pairs):
     return None
 
 
+def launches_per_step(n_pairs, scan_mode):
+    """Kernels one core-link step launches: k_zero (sp_reset); the scan
+    (k_scan, or per binning round k_bin + k_apply); the detect (k_fold8 after
+    a binned scan, k_detect, k_sort_emit).  Auto mode bins updates of 2^22
+    pairs and more, in rounds of up to 2^26 pairs."""
+    binned = scan_mode == 2 or (scan_mode == 0 and n_pairs >= (1 << 22))
+    if not binned:
+        return 1 + 1 + 2
+    rounds = max(1, -(-n_pairs // (1 << 26)))
+    return 1 + 2 * rounds + 1 + 2
+
+
 class ClockSampler:
     """nvidia-smi clocks/throttle sampling during the timed region."""
 
@@ -386,7 +398,7 @@ def run_ours(args):
                               "p99": det_sorted[min(len(det_sorted) - 1, int(0.99 * len(det_sorted)))]},
         "super_points": {"found": int(n_found), "planted_recall": recall},
         "clocks": clk,
-        "gpu_launches": 4 * K,
+        "gpu_launches": launches_per_step(n, args.scan_mode) * K,
         "cpu_baseline": cpu,
         "cpu_baseline_threads": cpu_threads,
         "e2e": e2e,
