@@ -96,9 +96,10 @@ extern "C" {
  * identical): SP_SCAN_AUTO (0) picks the binned form for updates of at least
  * 2^22 pairs when it applies (k <= 1024, LC >= 32, lr * LC <= 2^20), else the
  * direct form; SP_SCAN_DIRECT (1) sets every bit with an L2 atomic OR;
- * SP_SCAN_BINNED (2) sorts the pairs by LDC bit position, sets the bits of
- * each bit plane with shared-memory atomics and folds the planes into the
- * LDCA before the next detect, merge or export (when it applies).
+ * SP_SCAN_BINNED (2) groups the pairs' hips into lists by LDC bit position,
+ * sets the bits of each bit plane with shared-memory atomics and folds the
+ * planes into the LDCA before the next detect, merge or export (when it
+ * applies).
  * seed seeds the hash family: multiply-add-shift hashes whose (a, b) words are
  * consecutive SplitMix64 outputs for H1, H3, LH_0 .. LH_{lr-1}.
  */
