@@ -27,6 +27,10 @@
  *   - The library owns all sketch, staging and scratch memory of a context;
  *     it is allocated in sp_create() and released by sp_destroy().
  *   - A context is not thread safe: one host thread at a time.
+ *   - Every call that waits for the context's stream waits at most the
+ *     context's bound (sp_set_timeout, default 60 s) and then returns
+ *     SP_ERR_TIMEOUT with the work still in flight; only sp_destroy waits
+ *     without a bound.
  */
 #ifndef SUPERPOINT_H
 #define SUPERPOINT_H
@@ -52,7 +56,7 @@ extern "C" {
 #define SP_ERR_TRUNCATED (-3)        /* more results than the caller's cap; first cap written */
 #define SP_ERR_CANDIDATE_OVERFLOW (-4) /* device result or join bound exceeded; list incomplete */
 #define SP_ERR_CUDA (-5)             /* a CUDA runtime call failed */
-#define SP_ERR_TIMEOUT (-6)          /* a bounded wait gave up */
+#define SP_ERR_TIMEOUT (-6)          /* a wait for the stream passed the context's bound */
 #define SP_ERR_CHECKSUM (-7)         /* imported sketch image is corrupt or mismatched */
 #define SP_ERR_NOMEM (-8)            /* device or host allocation failed */
 #define SP_ERR_STATE (-9)            /* call not valid in the context's current state */
@@ -172,12 +176,25 @@ SP_API int sp_size_ldca(uint64_t n_pairs, uint32_t k_log2, uint64_t ldc_budget, 
  * Errors: SP_ERR_PARAM, SP_ERR_NOMEM, SP_ERR_CUDA.  *out is NULL on error. */
 SP_API int sp_create(const sp_params* p, void* cuda_stream, sp_ctx** out);
 
-/* Releases every resource of ctx after draining its stream.  NULL is a no-op. */
+/* Releases every resource of ctx after draining its stream (this wait has no
+ * bound).  NULL is a no-op. */
 SP_API void sp_destroy(sp_ctx* ctx);
 
 /* Replaces the context's stream (work already issued stays ordered on the old
  * one; the caller synchronises if needed). */
 SP_API int sp_set_stream(sp_ctx* ctx, void* cuda_stream);
+
+/* Bound of every wait of the context on its stream (sp_results, sp_detect,
+ * sp_export, sp_import, sp_autotune, and sp_update_batched when its ring of
+ * batch tables is full): a wait that has not seen the stream's work complete
+ * after timeout_ms milliseconds returns SP_ERR_TIMEOUT, leaving the work in
+ * flight (a later call may wait for it again; buffers the work reads or
+ * writes stay in use until it completes).  0 = wait without a bound.  The
+ * default of sp_create is 60,000 ms.  The paper has no counterpart: this is
+ * the failure detection of a watch point whose GPU stopped making progress,
+ * done on the host (the library's kernels never wait on a flag).  Errors:
+ * SP_ERR_PARAM (ctx NULL). */
+SP_API int sp_set_timeout(sp_ctx* ctx, uint32_t timeout_ms);
 
 /* Copy of the parameters the context was created with. */
 SP_API int sp_get_params(const sp_ctx* ctx, sp_params* out);
@@ -275,9 +292,12 @@ SP_API int sp_detect_async(sp_ctx* ctx, uint32_t router, uint32_t threshold);
  * host_out (may be NULL when cap = 0).  Errors: SP_ERR_TRUNCATED when
  * *n_total > cap; SP_ERR_CANDIDATE_OVERFLOW when the device result buffer
  * (max_candidates) or the join bound (max_join) overflowed, in which case the
- * list is incomplete; SP_ERR_TIMEOUT when a scan kernel of this context gave
- * up a bounded wait since the last check (the sketch is incomplete; no GPU
- * hang is possible); SP_ERR_STATE when no detect was issued; SP_ERR_CUDA. */
+ * list is incomplete; SP_ERR_ROUTER when a device batch table named a bad
+ * router or stream since the last check (that batch was skipped);
+ * SP_ERR_TIMEOUT when the wait for the stream passed the context's bound
+ * (sp_set_timeout; nothing was written, the detect is still in flight and a
+ * later sp_results may collect it); SP_ERR_STATE when no detect was issued;
+ * SP_ERR_CUDA. */
 SP_API int sp_results(sp_ctx* ctx, sp_candidate* host_out, uint64_t cap, uint64_t* n_total);
 
 /* Non-blocking form of sp_results for pipelines: enqueues on the stream the
@@ -316,13 +336,17 @@ SP_API int sp_slide(sp_ctx* ctx, uint32_t router);
  * b % 32 of word b / 32) -- followed by a 64-bit checksum.  With host_buf NULL
  * *n receives the image size.  A sliding context exports the bits of its
  * current window.  Synchronises the stream.
- * Errors: SP_ERR_TRUNCATED (cap too small), SP_ERR_ROUTER, SP_ERR_CUDA. */
+ * Errors: SP_ERR_TRUNCATED (cap too small), SP_ERR_ROUTER, SP_ERR_CUDA,
+ * SP_ERR_TIMEOUT (the copies into host_buf are still in flight: it stays in
+ * use until the stream passes them, and it holds no checksum). */
 SP_API int sp_export(sp_ctx* ctx, uint32_t router, void* host_buf, uint64_t cap, uint64_t* n);
 
 /* Loads an image written by sp_export into a router, replacing its sketch.
  * Rejects an image with a bad checksum or parameters other than the
  * context's (SP_ERR_CHECKSUM) without touching the router.  A sliding context
- * cannot import window bits (SP_ERR_STATE). */
+ * cannot import window bits (SP_ERR_STATE).  Synchronises the stream;
+ * SP_ERR_TIMEOUT leaves the copies from host_buf in flight (it stays in use
+ * until the stream passes them). */
 SP_API int sp_import(sp_ctx* ctx, uint32_t router, const void* host_buf, uint64_t n);
 
 /* Limits of sp_detect_noalloc. */
@@ -331,10 +355,11 @@ SP_API int sp_import(sp_ctx* ctx, uint32_t router, const void* host_buf, uint64_
 
 /* Detect without allocating.  The paper has no counterpart: this entry point
  * exists for callers that must not allocate device memory when they detect --
- * code recorded into a CUDA stream capture, programs whose device memory is
- * owned or budgeted by another allocator, and latency-critical loops that
- * cannot take an allocation (or its failure) on their path.  It runs the same
- * restore and filter as sp_detect_async on a sketch the caller holds:
+ * programs whose device memory is owned by another allocator (a framework's
+ * caching allocator, a partition fixed at start-up) or budgeted up front, and
+ * latency-critical loops that cannot take an allocation, or its failure, on
+ * their path.  It runs the same restore and filter as sp_detect_async on a
+ * sketch the caller holds:
  *   p          parameters the sketch was built with (validated; discrete
  *              window only; k_log2 <= SP_NOALLOC_MAX_K_LOG2)
  *   dev_seav   one router's SEAV, device memory, the sp_export layout
@@ -348,15 +373,17 @@ SP_API int sp_import(sp_ctx* ctx, uint32_t router, const void* host_buf, uint64_
  *              flags (1: more than cap found, 2: the join bound was hit)
  *   cuda_stream the stream the work is enqueued on (async)
  * It calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch
- * is one fixed array of about 556 KiB in the library's device image, held by
+ * is one fixed array of about 576 KiB in the library's device image, held by
  * every GPU that loads the library until the process exits.  The first call
- * on each device looks up that array's device address (cudaGetSymbolAddress
- * with the device current); make that first call before any stream capture.
- * All calls on a device share the array and it keeps the last call's contents
- * (each call resets what must start from zero): calls that overlap on the GPU
- * -- on different streams, or from different host threads -- race and give
- * undefined results.  Errors: SP_ERR_PARAM (a limit above exceeded, invalid
- * parameters, misaligned pointer), SP_ERR_CUDA; returns
+ * on each device sets the array up: it looks up the array's device address
+ * (cudaGetSymbolAddress, with the device current) and writes the estimate
+ * tables of every supported k into it with one synchronous copy; make that
+ * first call before any stream capture.  Later calls copy nothing from the
+ * host.  All calls on a device share the array and it keeps the last call's
+ * contents (each call resets what must start from zero): calls that overlap
+ * on the GPU -- on different streams, or from different host threads -- race
+ * and give undefined results.  Errors: SP_ERR_PARAM (a limit above exceeded,
+ * invalid parameters, misaligned pointer), SP_ERR_CUDA; returns
  * SP_WARN_THETA_BELOW_INIT like sp_detect_async. */
 SP_API int sp_detect_noalloc(const sp_params* p, const uint8_t* dev_seav, const uint32_t* dev_ldca,
                              uint32_t threshold, sp_candidate* dev_out, uint32_t cap,

@@ -8,7 +8,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <chrono>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "sp_internal.h"
@@ -27,6 +29,7 @@ constexpr uint64_t kBinnedRoundPairs = 1ull << 26;  // pairs per binning round
 // copies, so after the last copy only one round of 2^24 pairs is left to apply.
 constexpr uint64_t kHostRoundPairs = 1ull << 24;
 constexpr uint32_t kResultPrefix = 4096;            // records fetched with the status
+constexpr uint32_t kDefaultTimeoutMs = 60000;       // bound of every wait on the stream
 constexpr uint64_t kAlign = 256;
 
 uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
@@ -89,9 +92,11 @@ struct sp_ctx {
   uint64_t* keys = nullptr;                 // detect scratch: next_pow2(cap) keys
   sp_candidate* records = nullptr;          // sorted results, cap records
   DetectStatus* status = nullptr;
-  uint32_t* kerr = nullptr;                 // kernel error word (bounded waits)
+  uint32_t* kerr = nullptr;                 // kernel error word (bad device batch table entries)
   double* est_table = nullptr;              // -k ln(z / k), z = 0 .. k
   uint32_t cap = 0;
+  uint32_t timeout_ms = kDefaultTimeoutMs;  // 0: waits are unbounded
+  cudaEvent_t ev_wait = nullptr;            // marks the stream's work for a bounded wait
   bool detect_issued = false;
   uint32_t last_threshold = 0;
   // results: status, error word and the first kResultPrefix records land in
@@ -142,6 +147,36 @@ struct sp_ctx {
   uint32_t* wldca(uint32_t router) const { return reinterpret_cast<uint32_t*>(window + (uint64_t)router * stride + seav_pad); }
   uint32_t* ldca(uint32_t router) const { return reinterpret_cast<uint32_t*>(sketches + (uint64_t)router * stride + seav_pad); }
 };
+
+// Polls an event that was recorded on the context's stream until it has
+// completed, or until the context's bound has passed (SP_ERR_TIMEOUT; the
+// work stays in flight and a later wait may collect it).  No failure
+// detection of this kind is in the paper: it keeps a host thread from
+// waiting forever on a stream that stopped making progress.
+static int wait_event_bounded(const sp_ctx* ctx, cudaEvent_t ev) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (uint32_t polls = 0;; ++polls) {
+    const cudaError_t q = cudaEventQuery(ev);
+    if (q == cudaSuccess) return SP_OK;
+    if (q != cudaErrorNotReady) {
+      cudaGetLastError();
+      return SP_ERR_CUDA;
+    }
+    if (cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();   // not an error: keep launches' checks clean
+    if (ctx->timeout_ms) {
+      const auto waited = std::chrono::steady_clock::now() - t0;
+      if (waited >= std::chrono::milliseconds(ctx->timeout_ms)) return SP_ERR_TIMEOUT;
+    }
+    if (polls < 256) std::this_thread::yield();
+    else std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+// Bounded wait for all work issued on the context's stream so far.
+static int wait_stream(sp_ctx* ctx) {
+  if (cudaEventRecord(ctx->ev_wait, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+  return wait_event_bounded(ctx, ctx->ev_wait);
+}
 
 extern "C" {
 
@@ -311,6 +346,7 @@ void sp_destroy(sp_ctx* ctx) {
   cudaFree(ctx->status);
   cudaFree(ctx->kerr);
   cudaFree(ctx->est_table);
+  if (ctx->ev_wait) cudaEventDestroy(ctx->ev_wait);
   delete ctx;
 }
 
@@ -367,6 +403,7 @@ int sp_create(const sp_params* p, void* cuda_stream, sp_ctx** out) {
     cudaGetLastError();
     rc = SP_ERR_NOMEM;
   }
+  if (rc == SP_OK && cudaEventCreateWithFlags(&c->ev_wait, cudaEventDisableTiming) != cudaSuccess) rc = SP_ERR_CUDA;
   if (rc == SP_OK) {
     const uint32_t k = 1u << p->k_log2;
     double* table = static_cast<double*>(malloc((k + 1) * sizeof(double)));
@@ -399,7 +436,7 @@ int sp_create(const sp_params* p, void* cuda_stream, sp_ctx** out) {
         cudaMalloc(&c->window, c->stride * p->n_routers) != cudaSuccess) { cudaGetLastError(); rc = SP_ERR_NOMEM; }
     else if (sp::launch_zero(c->stamps, c->st_stride * p->n_routers, c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
   }
-  if (rc == SP_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
+  if (rc == SP_OK) rc = wait_stream(c);
   if (rc != SP_OK) {
     sp_destroy(c);
     return rc;
@@ -411,6 +448,12 @@ int sp_create(const sp_params* p, void* cuda_stream, sp_ctx** out) {
 int sp_set_stream(sp_ctx* ctx, void* cuda_stream) {
   if (!ctx) return SP_ERR_PARAM;
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  return SP_OK;
+}
+
+int sp_set_timeout(sp_ctx* ctx, uint32_t timeout_ms) {
+  if (!ctx) return SP_ERR_PARAM;
+  ctx->timeout_ms = timeout_ms;
   return SP_OK;
 }
 
@@ -439,6 +482,7 @@ static int ensure_binned(sp_ctx* ctx, uint32_t router) {
     const uint32_t chunks = (uint32_t)((ctx->bs.max_pairs + kStagingPairs - 1) / kStagingPairs);
     const uint64_t cap = sp::binned_list_cap(ctx->bs.max_pairs, bins, ctx->bs.ctas, chunks);
     if ((uint64_t)bins * ctx->bs.ctas * cap >= (1ull << 32)) return SP_ERR_PARAM;   // 32-bit list slots
+    ctx->bs.cap_alloc = (uint32_t)cap;
     if (cudaMalloc(&ctx->bs.lists, (uint64_t)bins * ctx->bs.ctas * cap * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&ctx->bs.counts, (uint64_t)bins * ctx->bs.ctas * sizeof(uint32_t)) != cudaSuccess) {
       cudaGetLastError();
@@ -611,7 +655,8 @@ static bool capturing(cudaStream_t st) {
 static int upload_table(sp_ctx* ctx, const sp_batch* tab, uint32_t n, const sp_batch** dev) {
   sp_ctx::TableSlot& t = ctx->tables[ctx->table_next++ % sp_ctx::kTableRing];
   if (n > t.cap) {
-    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;   // old copy no longer read
+    const int wrc = wait_stream(ctx);                                        // old copy no longer read
+    if (wrc != SP_OK) return wrc;
     if (t.host) cudaFreeHost(t.host);
     cudaFree(t.dev);
     t.host = nullptr;
@@ -624,7 +669,10 @@ static int upload_table(sp_ctx* ctx, const sp_batch* tab, uint32_t n, const sp_b
     t.cap = cap;
   }
   if (!t.ev && cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming) != cudaSuccess) return SP_ERR_CUDA;
-  if (t.pending && cudaEventSynchronize(t.ev) != cudaSuccess) return SP_ERR_CUDA;
+  if (t.pending) {
+    const int wrc = wait_event_bounded(ctx, t.ev);
+    if (wrc != SP_OK) return wrc;
+  }
   memcpy(t.host, tab, n * sizeof(sp_batch));
   if (cudaMemcpyAsync(t.dev, t.host, n * sizeof(sp_batch), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
       cudaEventRecord(t.ev, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
@@ -681,9 +729,15 @@ int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
         ++i;
         continue;
       }
+      // a round ends before its pairs pass max_pairs or its list capacity
+      // (which grows with the binning launches) passes the allocated one
       size_t j = i;
       uint64_t sum = 0;
-      while (j < mine.size() && sum + n_pairs[mine[j]] <= ctx->bs.max_pairs) sum += n_pairs[mine[j++]];
+      while (j < mine.size() && sum + n_pairs[mine[j]] <= ctx->bs.max_pairs) {
+        const uint32_t l = (uint32_t)((j + 1 - i + sp::kBinMaxSrc - 1) / sp::kBinMaxSrc);
+        if (j > i && sp::binned_list_cap(sum + n_pairs[mine[j]], bins, ctx->bs.ctas, l) > ctx->bs.cap_alloc) break;
+        sum += n_pairs[mine[j++]];
+      }
       // the round's batches, up to kBinMaxSrc streams per binning launch
       const uint32_t launches = (uint32_t)((j - i + sp::kBinMaxSrc - 1) / sp::kBinMaxSrc);
       const uint32_t cap = sp::binned_list_cap(sum, bins, ctx->bs.ctas, launches);
@@ -751,10 +805,9 @@ int sp_autotune(sp_ctx* ctx, const uint32_t* dev_pairs, uint64_t n_pairs, uint32
         if ((rc = launch_table(ctx, dev_tab, 1)) != SP_OK) break;
       cudaEventRecord(e1, ctx->stream);
       float ms = 0.f;
-      if (rc != SP_OK || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-        rc = rc != SP_OK ? rc : SP_ERR_CUDA;
-        break;
-      }
+      if (rc == SP_OK) rc = wait_event_bounded(ctx, e1);
+      if (rc == SP_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = SP_ERR_CUDA;
+      if (rc != SP_OK) break;
       if (ms < best) { best = ms; bt = t; bg = ctx->multi_grid; }
     }
     if (rc != SP_OK) break;
@@ -767,7 +820,7 @@ int sp_autotune(sp_ctx* ctx, const uint32_t* dev_pairs, uint64_t n_pairs, uint32
   if (best_threads) *best_threads = (uint32_t)bt;
   if (best_blocks) *best_blocks = (uint32_t)(bg / (sms ? sms : 1));
   rc = sp_reset(ctx, 0);
-  if (rc == SP_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = SP_ERR_CUDA;
+  if (rc == SP_OK) rc = wait_stream(ctx);
   return rc;
 }
 
@@ -842,18 +895,18 @@ int sp_results(sp_ctx* ctx, sp_candidate* host_out, uint64_t cap, uint64_t* n_to
       cudaMemcpyAsync(ctx->result_host + kKerrAt, ctx->kerr, sizeof(uint32_t), cudaMemcpyDeviceToHost,
                       ctx->stream) != cudaSuccess ||
       (pre && cudaMemcpyAsync(ctx->result_host + kRecordsAt, ctx->records, pre * sizeof(sp_candidate),
-                              cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) ||
-      cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+                              cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)) return SP_ERR_CUDA;
+  int wrc = wait_stream(ctx);
+  if (wrc != SP_OK) return wrc;
   DetectStatus st;
   uint32_t kerr = 0;
   memcpy(&st, ctx->result_host, sizeof(st));
   memcpy(&kerr, ctx->result_host + kKerrAt, sizeof(kerr));
   if (kerr) {
-    // bit 0: a scan kernel gave up a bounded wait (the sketch is incomplete);
-    // bit 1: a device batch table named a bad router or stream (batch skipped)
+    // a device batch table named a bad router or stream (the batch was skipped)
     cudaMemsetAsync(ctx->kerr, 0, sizeof(uint32_t), ctx->stream);
     *n_total = st.count;
-    return (kerr & 1u) ? SP_ERR_TIMEOUT : SP_ERR_ROUTER;
+    return SP_ERR_ROUTER;
   }
   *n_total = st.count;
   const uint64_t avail = st.count < ctx->cap ? st.count : ctx->cap;
@@ -862,8 +915,8 @@ int sp_results(sp_ctx* ctx, sp_candidate* host_out, uint64_t cap, uint64_t* n_to
   if (staged) memcpy(host_out, ctx->result_host + kRecordsAt, staged * sizeof(sp_candidate));
   if (m > staged) {
     if (cudaMemcpyAsync(host_out + staged, ctx->records + staged, (m - staged) * sizeof(sp_candidate),
-                        cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
-        cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+                        cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+    if ((wrc = wait_stream(ctx)) != SP_OK) return wrc;
   }
   if (st.overflow) return SP_ERR_CANDIDATE_OVERFLOW;
   if (st.count > cap) return SP_ERR_TRUNCATED;
@@ -939,8 +992,9 @@ int sp_export(sp_ctx* ctx, uint32_t router, void* host_buf, uint64_t cap, uint64
   memcpy(out, &h, sizeof(h));
   if (cudaMemcpyAsync(out + sizeof(h), seav, ctx->seav_bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
       cudaMemcpyAsync(out + sizeof(h) + ctx->seav_bytes, ldca, ctx->ldca_bytes, cudaMemcpyDeviceToHost,
-                      ctx->stream) != cudaSuccess ||
-      cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+                      ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+  const int wrc = wait_stream(ctx);
+  if (wrc != SP_OK) return wrc;
   const uint64_t sum = fnv1a64(out, total - 8);
   memcpy(out + total - 8, &sum, 8);
   return SP_OK;
@@ -966,9 +1020,9 @@ int sp_import(sp_ctx* ctx, uint32_t router, const void* host_buf, uint64_t n) {
     return SP_ERR_CHECKSUM;
   ctx->planes_dirty[router] = false;
   if (cudaMemcpyAsync(ctx->seav(router), in + sizeof(h), ctx->seav_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
-      cudaMemcpyAsync(ctx->ldca(router), in + sizeof(h) + ctx->seav_bytes, ctx->ldca_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
-      cudaStreamSynchronize(ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
-  return SP_OK;
+      cudaMemcpyAsync(ctx->ldca(router), in + sizeof(h) + ctx->seav_bytes, ctx->ldca_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+    return SP_ERR_CUDA;
+  return wait_stream(ctx);
 }
 
 }  // extern "C"

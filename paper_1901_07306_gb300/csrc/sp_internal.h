@@ -72,6 +72,7 @@ struct BinnedScratch {
   uint32_t* planes = nullptr;   // plane accumulator of one router, [ceil(W / 8)][k][8] words, W = LR * LC / 32
   bool accumulate = false;      // planes hold earlier bits (load instead of zero)
   uint32_t ctas = 0;            // persistent binning blocks
+  uint32_t cap_alloc = 0;       // hips per list the allocation holds: every launch's cap is clamped to it
   uint64_t max_pairs = 0;       // pairs per binning round the lists are sized for
   int fold_grid = 0;
 };

@@ -3,12 +3,12 @@
 // sp_detect_noalloc runs the same restore-and-filter kernels as
 // sp_detect_async, but on a sketch the caller already holds in device memory
 // and with all of its scratch (the unsorted result keys, the status word and
-// the estimate table) taken from one fixed array in this file instead of from
-// a context.  It exists for callers that may not allocate device memory at
-// the point where they detect: code running inside a stream capture that must
-// not call cudaMalloc, processes whose device memory is owned by another
-// allocator or budgeted up front, and real-time loops that cannot afford an
-// allocation (or its failure) on their critical path.
+// the estimate tables) taken from one fixed array in this file instead of
+// from a context.  It exists for callers that may not allocate device memory
+// at the point where they detect: processes whose device memory is owned by
+// another allocator (a framework's caching allocator, a partition fixed at
+// start-up) or budgeted up front, and real-time loops that cannot afford an
+// allocation, or its failure, on their critical path.
 #include <math.h>
 #include <string.h>
 
@@ -20,34 +20,57 @@ namespace {
 
 // Scratch layout, in 64-bit words:
 //   [0, kKeys)                unsorted (ip << 32 | z0) keys, a power of two
-//   [kKeys, kKeys + kEst)     estimate table -k ln(z / k), z = 0 .. k (doubles)
-//   [kKeys + kEst, + 2)       DetectStatus
+//   [kKeys, kKeys + kEstAll)  estimate tables -k ln(z / k), z = 0 .. k (doubles),
+//                             one per k_log2 = 5 .. SP_NOALLOC_MAX_K_LOG2,
+//                             written once per device at set-up
+//   [kKeys + kEstAll, + 2)    DetectStatus
 constexpr uint32_t kKeys = SP_NOALLOC_MAX_RESULTS;            // 65536
-constexpr uint32_t kEst = (1u << SP_NOALLOC_MAX_K_LOG2) + 1;  // 4097
-constexpr uint32_t kWords = kKeys + kEst + 2;
+constexpr uint32_t kMinKLog2 = 5;
+// table of k_log2 = q starts at sum over q' < q of (2^q' + 1) doubles
+constexpr uint32_t est_offset(uint32_t q) { return ((1u << q) - (1u << kMinKLog2)) + (q - kMinKLog2); }
+constexpr uint32_t kEstAll = est_offset(SP_NOALLOC_MAX_K_LOG2 + 1);   // 8168
+constexpr uint32_t kWords = kKeys + kEstAll + 2;
 
-// Every GPU that loads the library holds this array (about 556 KiB) until
+// Every GPU that loads the library holds this array (about 576 KiB) until
 // the process exits.  All calls on a device share it.
 static __device__ __align__(256) uint64_t sp_noalloc_scratch[kWords];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 uint64_t* g_scratch[kMaxDevices] = {};     // device address of the array, per device
+double g_tables[kEstAll];                  // host copy of the estimate tables (static storage)
+bool g_tables_ready = false;
 
 // The host-side name sp_noalloc_scratch is only a stand-in; the device
 // address comes from cudaGetSymbolAddress, once per device, with that device
-// current.
+// current.  The same set-up writes the estimate tables of every supported k
+// into the array (one synchronous copy from static host memory), so later
+// calls copy nothing from the host.
 int scratch_for_current_device(uint64_t** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SP_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch[dev]) {
+    if (!g_tables_ready) {
+      for (uint32_t q = kMinKLog2; q <= SP_NOALLOC_MAX_K_LOG2; ++q) {
+        double* t = g_tables + est_offset(q);
+        const uint32_t k = 1u << q;
+        t[0] = (double)k * log((double)k);   // saturated union: reported as k ln k
+        for (uint32_t z = 1; z <= k; ++z) t[z] = -(double)k * log((double)z / (double)k);   // Eq. 4
+      }
+      g_tables_ready = true;
+    }
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, sp_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return SP_ERR_CUDA;
     }
-    g_scratch[dev] = static_cast<uint64_t*>(p);
+    uint64_t* base = static_cast<uint64_t*>(p);
+    if (cudaMemcpy(base + kKeys, g_tables, sizeof(g_tables), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      return SP_ERR_CUDA;
+    }
+    g_scratch[dev] = base;
   }
   *out = g_scratch[dev];
   return SP_OK;
@@ -103,19 +126,13 @@ extern "C" int sp_detect_noalloc(const sp_params* p, const uint8_t* dev_seav, co
   d.ldca_words /= 4;
 
   uint64_t* keys = scratch;
-  double* est = reinterpret_cast<double*>(scratch + kKeys);
-  sp::DetectStatus* status = reinterpret_cast<sp::DetectStatus*>(scratch + kKeys + kEst);
+  const double* est = reinterpret_cast<const double*>(scratch + kKeys) + est_offset(p->k_log2);
+  sp::DetectStatus* status = reinterpret_cast<sp::DetectStatus*>(scratch + kKeys + kEstAll);
 
-  // the array keeps the previous call's contents: reset the status word and
-  // rewrite the estimate table for this call's k (keys are written before
-  // they are read, up to the count in the status word)
-  double table[kEst];
-  const uint32_t k = 1u << p->k_log2;
-  table[0] = (double)k * log((double)k);
-  for (uint32_t z = 1; z <= k; ++z) table[z] = -(double)k * log((double)z / (double)k);
-  if (cudaMemsetAsync(status, 0, sizeof(sp::DetectStatus), st) != cudaSuccess ||
-      cudaMemcpyAsync(est, table, (k + 1) * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return SP_ERR_CUDA;
+  // the array keeps the previous call's contents: reset the status word (keys
+  // are written before they are read, up to the count in the status word;
+  // the estimate tables never change after set-up)
+  if (cudaMemsetAsync(status, 0, sizeof(sp::DetectStatus), st) != cudaSuccess) return SP_ERR_CUDA;
   if (cap == 0) cap = 1;   // the kernels need room for one key; nothing is copied out
   const uint32_t zt = sp_z_theta(p->k_log2, threshold ? threshold : p->theta);
   const uint64_t max_join = p->max_join ? p->max_join : (1ull << 26);

@@ -527,6 +527,9 @@ BinSrc bin_src_one(const uint32_t* pairs, uint64_t n_pairs) {
 cudaError_t binned_bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const BinSrc& src,
                              const BinnedScratch& s, uint32_t cap, bool append, uint32_t rot, cudaStream_t st) {
   if (src.count == 0) return cudaSuccess;
+  // the list stride never exceeds what was allocated (hips past a full list go
+  // to L2 REDs, so a smaller cap only costs speed)
+  if (cap > s.cap_alloc) cap = s.cap_alloc;
   switch (d.lr) {
     case 1: return bin_chunk<1>(d, seav, ldca, src, s, cap, append, rot, st);
     case 2: return bin_chunk<2>(d, seav, ldca, src, s, cap, append, rot, st);
@@ -541,6 +544,7 @@ cudaError_t binned_bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, 
 
 cudaError_t binned_apply_round(const DevParams& d, const BinnedScratch& s, uint32_t cap, bool accumulate,
                                cudaStream_t st) {
+  if (cap > s.cap_alloc) cap = s.cap_alloc;          // the same clamp as the round's binning launches
   switch (d.lr) {
     case 1: return apply_round<1>(d, s, cap, accumulate, st);
     case 2: return apply_round<2>(d, s, cap, accumulate, st);

@@ -18,6 +18,15 @@ Engine (``SketchServer.run``):
     asynchronously, and the routers start the next window (reset, or slide
     when ``window_slices`` > 1, Sec. 5).  A request belongs to the window in
     which it was admitted, so window contents depend only on arrival order.
+  * failure detection -- every device wait of the engine (a step's scan, a
+    window's detection) is bounded: when the oldest outstanding one has not
+    completed ``timeout_s`` after it was issued, ``run`` raises
+    ``ServingTimeout`` (the paper has no such step; a watch point whose GPU
+    stopped making progress is reported instead of waited on forever).
+
+The device side sits behind ``GpuOps`` (context, streams, staging arenas),
+so the scheduling, admission and deadline logic of ``SketchServer`` can also
+be driven by a stand-in with the same methods.
 
 Latencies are host wall-clock times: ``ack`` = arrival to the moment its scan
 is seen complete; ``result`` = arrival to the moment the detection of its
@@ -26,12 +35,11 @@ window is available on the host.
 from __future__ import annotations
 
 import time
-from dataclasses import dataclass, field
+from collections import deque
+from dataclasses import dataclass
 
 import numpy as np
 import torch
-
-from . import sp
 
 
 @dataclass
@@ -40,7 +48,6 @@ class Request:
     pairs: torch.Tensor          # pinned host int32 tensor of 2 n values
     arrival: float               # seconds after the start of the run
     window: int = -1
-    _slot: object = None         # this request's slice of a staging arena
     t_ack: float = float("nan")
     t_result: float = float("nan")
 
@@ -62,11 +69,14 @@ class WindowResult:
     t_ready: float = float("nan")
 
 
+class ServingTimeout(TimeoutError):
+    """A device wait of the server passed its bound; the work is still in
+    flight and the server cannot be reused (``close`` waits for the device)."""
+
+
 class _Budget:
     """Admission by a fixed device-memory budget: bytes of admitted requests
-    whose scan has not completed yet.  Device buffers come from PyTorch's
-    caching allocator and are released only after the scan that reads them
-    has been seen complete."""
+    whose scan has not completed yet."""
 
     def __init__(self, budget_bytes: int):
         self.budget = int(budget_bytes)
@@ -84,18 +94,17 @@ class _Budget:
         self.in_use -= nbytes
 
 
-class SketchServer:
-    """Routers 0 .. n_routers-1 plus the global router n_routers, one context.
+class GpuOps:
+    """The server's device side: one library context holding routers
+    0 .. n_routers - 1 plus the global router n_routers, a compute and a copy
+    stream, and (batched engine) two staging arenas of half the budget each:
+    step s fills arena s % 2 and may reuse it once the scan of step s - 2 has
+    completed."""
 
-    batched=True is the continuous-batching engine described above;
-    batched=False is the plain path: every request is copied and scanned on
-    its own (one sp_update_host per request) as soon as it arrives, with the
-    same windows, so both paths produce the same detection results.
-    """
-
-    def __init__(self, n_routers: int, params: dict | None = None, budget_bytes: int = 1 << 30,
-                 detect_every: int = 1 << 24, window_slices: int = 1, max_step_requests: int = 1024,
-                 report_cap: int = 4096, batched: bool = True):
+    def __init__(self, n_routers: int, params: dict | None, budget_bytes: int, window_slices: int,
+                 batched: bool, report_cap: int):
+        from . import sp
+        self.sp = sp
         self.n_routers = n_routers
         self.gs = n_routers                                  # the global server's router slot
         kw = dict(params or {})
@@ -103,25 +112,59 @@ class SketchServer:
         self.compute = torch.cuda.Stream()
         self.copy = torch.cuda.Stream()
         self.ctx = sp.SuperPoint(sp.make_params(**kw), stream=self.compute)
-        self.budget = _Budget(budget_bytes)
-        # two staging arenas of half the budget each: step s fills arena s % 2
-        # and may reuse it once the scan of step s - 2 has completed
         half = (int(budget_bytes) // 2) // 8 * 2             # int32 words, whole pairs
         self.arenas = [torch.empty(half, dtype=torch.int32, device="cuda") for _ in range(2)] if batched else []
         self.arena_free = [None, None]                        # event of the last step that read the arena
-        self.detect_every = int(detect_every)
         self.window_slices = window_slices
-        self.max_step = max_step_requests
-        self.report_cap = report_cap
         self.batched = batched
-        self.windows: list[WindowResult] = []
+        self.report_cap = report_cap
 
     def close(self):
         self.ctx.close()
 
-    # -- window end: merge into the global router, detect, start the next ----
-    def _close_window(self, index: int, n_pairs: int):
-        c = self.ctx.ctx
+    def synchronize(self):
+        torch.cuda.synchronize()
+
+    def arena_words(self) -> int:
+        """int32 words of one staging arena (0: the plain path stages nothing)."""
+        return self.arenas[0].numel() if self.batched else 0
+
+    def arena_ready(self, arena: int) -> bool:
+        return not self.batched or self.arena_free[arena] is None or self.arena_free[arena].query()
+
+    def issue_step(self, step: list, arena: int, offsets: list):
+        """Copies the step's requests into the arena (at the given word
+        offsets) and scans them with one batched call (batched engine), or
+        copies and scans each on its own (plain path).  Returns the event
+        that completes with the step's scan."""
+        sp, c = self.sp, self.ctx.ctx
+        if self.batched:
+            bufs = [self.arenas[arena][o:o + r.pairs.numel()] for r, o in zip(step, offsets)]
+            with torch.cuda.stream(self.copy):
+                if self.arena_free[arena] is not None:
+                    self.copy.wait_event(self.arena_free[arena])
+                for r, b in zip(step, bufs):
+                    b.copy_(r.pairs, non_blocking=True)
+                copied = torch.cuda.Event()
+                copied.record(self.copy)
+            self.compute.wait_event(copied)
+            with torch.cuda.stream(self.compute):
+                sp.sp_update_batched(c, [r.router for r in step], bufs)
+        else:
+            with torch.cuda.stream(self.compute):
+                for r in step:                                # one copy + one launch each
+                    sp.sp_update_host(c, r.router, r.pairs)
+        ev = torch.cuda.Event()
+        ev.record(self.compute)
+        if self.batched:
+            self.arena_free[arena] = ev
+        return ev
+
+    def close_window(self):
+        """Window end: OR-merge the routers into the global router, detect it
+        asynchronously (results copied to pinned host memory), start the next
+        window.  Returns (event, handle for read_window)."""
+        sp, c = self.sp, self.ctx.ctx
         with torch.cuda.stream(self.compute):
             sp.sp_merge(c, list(range(self.n_routers)), self.gs)
             sp.sp_detect_async(c, self.gs, 0)
@@ -136,57 +179,99 @@ class SketchServer:
                     sp.sp_reset(c, r)
             ev = torch.cuda.Event()
             ev.record(self.compute)
-        return ev, WindowResult(index=index, n_pairs=n_pairs), out_t, status
+        return ev, (out_t, status)
+
+    def read_window(self, handle):
+        """(super points found, their records) of a completed detection."""
+        out_t, status = handle
+        cnt, _flags = (int(x) for x in status.numpy().view(np.uint32))
+        return cnt, out_t.numpy().view(self.sp.CANDIDATE)[:min(cnt, self.report_cap)].copy()
+
+
+class SketchServer:
+    """Routers 0 .. n_routers-1 plus the global router n_routers, one context.
+
+    batched=True is the continuous-batching engine described above;
+    batched=False is the plain path: every request is copied and scanned on
+    its own (one sp_update_host per request) as soon as it arrives, with the
+    same windows, so both paths produce the same detection results.
+    ``ops`` replaces the device side (default: a ``GpuOps`` on the current
+    GPU); ``timeout_s`` bounds every device wait.
+    """
+
+    def __init__(self, n_routers: int, params: dict | None = None, budget_bytes: int = 1 << 30,
+                 detect_every: int = 1 << 24, window_slices: int = 1, max_step_requests: int = 1024,
+                 report_cap: int = 4096, batched: bool = True, timeout_s: float = 60.0, ops=None):
+        self.n_routers = n_routers
+        self.budget = _Budget(budget_bytes)
+        self.detect_every = int(detect_every)
+        self.max_step = max_step_requests
+        self.batched = batched
+        self.timeout_s = float(timeout_s)
+        self.ops = ops if ops is not None else GpuOps(n_routers, params, budget_bytes, window_slices, batched,
+                                                      report_cap)
+        self.windows: list[WindowResult] = []
+        self.elapsed = float("nan")
+
+    def close(self):
+        self.ops.close()
 
     def run(self, requests: list[Request]):
-        """Serves the requests (sorted by arrival); returns self.windows."""
-        from collections import deque
-        c = self.ctx.ctx
+        """Serves the requests (sorted by arrival); returns self.windows.
+        Raises ServingTimeout when a step's scan or a window's detection has
+        not completed timeout_s after it was issued."""
+        ops = self.ops
         pending = deque(sorted(requests, key=lambda r: r.arrival))
-        steps = deque()           # (event, requests, device buffers, bytes)
-        detects = deque()         # (event, WindowResult, pinned records, pinned status, requests)
+        steps = deque()           # (event, issued at, requests, bytes, step index)
+        detects = deque()         # (event, issued at, WindowResult, handle, requests)
         window, window_pairs, window_reqs = 0, 0, []
-        steps_done_or_issued = []                 # one entry per issued step (its parity picks the arena)
-        torch.cuda.synchronize()
+        n_steps = 0
+        arena_words = ops.arena_words()
+        ops.synchronize()
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0  # noqa: E731
         while pending or steps or detects:
             progressed = False
             while steps and steps[0][0].query():                     # scans done: ack, free
-                _, reqs, bufs, nbytes = steps.popleft()
+                _, _, reqs, nbytes, _ = steps.popleft()
                 t = now()
                 for r in reqs:
                     r.t_ack = t
-                    r._slot = None
                 self.budget.give(nbytes)
                 progressed = True
             while detects and detects[0][0].query():                 # detections on the host
-                _, res, out_t, status, reqs = detects.popleft()
+                _, _, res, handle, reqs = detects.popleft()
                 t = now()
-                cnt, flags = (int(x) for x in status.numpy().view(np.uint32))
-                res.n_found = cnt
-                res.records = out_t.numpy().view(sp.CANDIDATE)[:min(cnt, self.report_cap)].copy()
+                res.n_found, res.records = ops.read_window(handle)
                 res.t_ready = t
                 for r in reqs:
                     r.t_result = t
                 self.windows.append(res)
                 progressed = True
+            # the stream runs in order: the oldest outstanding wait is the first to pass its bound
+            t = now()
+            if steps and t - steps[0][1] > self.timeout_s:
+                raise ServingTimeout(f"the scan of step {steps[0][4]} ({len(steps[0][2])} requests) has not "
+                                     f"completed {self.timeout_s:g} s after it was issued")
+            if detects and t - detects[0][1] > self.timeout_s:
+                raise ServingTimeout(f"the detection of window {detects[0][2].index} has not completed "
+                                     f"{self.timeout_s:g} s after it was issued")
             # admit what has arrived, in order, within the budget and the window
-            step = []
+            step, offsets = [], []
             boundary = False
-            arena = len(steps_done_or_issued) % 2 if self.batched else 0
-            arena_ready = not self.batched or self.arena_free[arena] is None or self.arena_free[arena].query()
+            arena = n_steps % 2 if self.batched else 0
+            arena_ready = ops.arena_ready(arena)
             used = 0
             while arena_ready and pending and pending[0].arrival <= now() and len(step) < self.max_step \
                     and self.budget.fits(pending[0].nbytes):
                 r = pending[0]
                 if self.batched:
                     words = r.pairs.numel()
-                    if words > self.arenas[arena].numel():
+                    if words > arena_words:
                         raise ValueError(f"a {r.nbytes}-byte request exceeds half the staging budget")
-                    if used + words > self.arenas[arena].numel():
+                    if used + words > arena_words:
                         break                                         # this step's arena is full
-                    r._slot = self.arenas[arena][used:used + words]
+                    offsets.append(used)
                     used += words
                 pending.popleft()
                 self.budget.take(r.nbytes)                            # charged as it is admitted
@@ -200,39 +285,18 @@ class SketchServer:
             if not pending and window_reqs and not step and not boundary:
                 boundary = True                                       # the last, partial window
             if step:
-                nbytes = sum(r.nbytes for r in step)
-                if self.batched:
-                    with torch.cuda.stream(self.copy):
-                        if self.arena_free[arena] is not None:
-                            self.copy.wait_event(self.arena_free[arena])
-                        for r in step:
-                            r._slot.copy_(r.pairs, non_blocking=True)
-                        copied = torch.cuda.Event()
-                        copied.record(self.copy)
-                    self.compute.wait_event(copied)
-                    bufs = [r._slot for r in step]
-                    with torch.cuda.stream(self.compute):
-                        sp.sp_update_batched(c, [r.router for r in step], bufs)
-                else:
-                    bufs = []
-                    with torch.cuda.stream(self.compute):
-                        for r in step:                                # one copy + one launch each
-                            sp.sp_update_host(c, r.router, r.pairs)
-                ev = torch.cuda.Event()
-                ev.record(self.compute)
-                if self.batched:
-                    self.arena_free[arena] = ev
-                steps.append((ev, step, bufs, nbytes))
-                steps_done_or_issued.append(None)
+                ev = ops.issue_step(step, arena, offsets)
+                steps.append((ev, now(), step, sum(r.nbytes for r in step), n_steps))
+                n_steps += 1
                 progressed = True
             if boundary:
-                ev, res, out_t, status = self._close_window(window, window_pairs)
-                detects.append((ev, res, out_t, status, window_reqs))
+                ev, handle = ops.close_window()
+                detects.append((ev, now(), WindowResult(index=window, n_pairs=window_pairs), handle, window_reqs))
                 window, window_pairs, window_reqs = window + 1, 0, []
                 progressed = True
             if not progressed:
                 time.sleep(20e-6)
-        torch.cuda.synchronize()
+        ops.synchronize()
         self.elapsed = now()
         return self.windows
 
@@ -253,8 +317,9 @@ def poisson_requests(seed: int, n_routers: int, n_requests: int, rate_pairs_per_
         n = int(sizes[i])
         pairs = (streams(int(routers[i]), n, seed * 100003 + i) if streams is not None
                  else W.uniform_pairs(n, seed=seed * 100003 + i, n_hosts=max(1, n // 4)))
-        t = torch.from_numpy(np.ascontiguousarray(pairs, np.uint32).reshape(-1).view(np.int32)).pin_memory()
-        out.append(Request(router=int(routers[i]), pairs=t, arrival=float(arrivals[i])))
+        t = torch.from_numpy(np.ascontiguousarray(pairs, np.uint32).reshape(-1).view(np.int32))
+        out.append(Request(router=int(routers[i]), pairs=t.pin_memory() if torch.cuda.is_available() else t,
+                           arrival=float(arrivals[i])))
     return out
 
 

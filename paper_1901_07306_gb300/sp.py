@@ -41,7 +41,7 @@ EXPORTED = (
     "sp_reset", "sp_update", "sp_update_host", "sp_update_batched", "sp_merge",
     "sp_detect_async", "sp_results", "sp_detect", "sp_results_device", "sp_slide",
     "sp_export", "sp_import", "sp_detect_noalloc", "sp_update_batched_device", "sp_autotune",
-    "sp_results_async", "sp_psu", "sp_size_ldca",
+    "sp_results_async", "sp_psu", "sp_size_ldca", "sp_set_timeout",
 )
 
 
@@ -93,6 +93,7 @@ def _load():
         "sp_create": (i32, [P(sp_params), vp, P(vp)]),
         "sp_destroy": (None, [vp]),
         "sp_set_stream": (i32, [vp, vp]),
+        "sp_set_timeout": (i32, [vp, u32]),
         "sp_get_params": (i32, [vp, P(sp_params)]),
         "sp_reset": (i32, [vp, u32]),
         "sp_update": (i32, [vp, u32, vp, u64]),
@@ -205,6 +206,10 @@ def sp_destroy(ctx: int) -> None:
 
 def sp_set_stream(ctx: int, stream) -> None:
     _check(lib.sp_set_stream(ctypes.c_void_p(ctx), ctypes.c_void_p(_stream_handle(stream))), "sp_set_stream")
+
+
+def sp_set_timeout(ctx: int, timeout_ms: int) -> None:
+    _check(lib.sp_set_timeout(ctypes.c_void_p(ctx), timeout_ms), "sp_set_timeout")
 
 
 def sp_get_params(ctx: int) -> sp_params:

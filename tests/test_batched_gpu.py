@@ -194,3 +194,29 @@ def test_many_batches_of_one_router_binned(sp, torch):
         assert same_sketch(ctx, osk, 1)
         seav, ldca = ctx.sketch_image(0)
         assert not seav.any() and not ldca.any()
+
+
+@pytest.mark.parametrize("n_batches,lo,hi", [(2048, 4096, 4096), (3000, 500, 6000)])
+def test_thousands_of_small_batches_of_one_router(sp, torch, n_batches, lo, hi):
+    """Thousands of small batches of one router in one call (> 2^22 pairs in
+    total, so the router takes the binned rounds): the rounds must stay
+    within the allocated list capacity whatever the number of binning
+    launches they need, and the sketch and result list stay bit-exact."""
+    kw = dict(theta=1024, seed=17, n_routers=2, scan_mode=0)
+    rng = np.random.default_rng(17)
+    sizes = rng.integers(lo, hi + 1, n_batches)
+    assert sizes.sum() >= (1 << 22)
+    pairs, planted = W.single_window(seed=17, n=int(sizes.sum()), n_background=1 << 17, n_planted=8,
+                                     planted_degree=3000)
+    flat = dev(torch, pairs)
+    cuts = np.concatenate([[0], np.cumsum(sizes)])
+    tensors = [flat[2 * int(a):2 * int(b)] for a, b in zip(cuts[:-1], cuts[1:])]
+    with sp.SuperPoint(**kw) as ctx:
+        sp.sp_update_batched(ctx.ctx, [1] * n_batches, tensors)
+        osk = O.Sketch(oparams(kw)).update(pairs)
+        assert same_sketch(ctx, osk, 1)
+        got, n, rc = ctx.detect(router=1)
+        want, n_want, _ = osk.detect()
+        assert rc == sp.SP_OK and n == n_want
+        assert np.array_equal(got["ip"], want["ip"]) and np.array_equal(got["z0"], want["z0"])
+        assert set(planted.tolist()) <= set(got["ip"].tolist())

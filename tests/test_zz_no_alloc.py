@@ -1,9 +1,9 @@
 """sp_detect_noalloc: detect with no device allocation, for callers that may
-not allocate at that point (stream capture, externally budgeted device
-memory, latency-critical loops).  Its output must equal the context-based
-sp_detect on the same sketch, bit for bit, call after call: the scratch
-array it shares across calls keeps the previous contents, so a stale status
-or table would show up on the second call.
+not allocate at that point (device memory owned by another allocator or
+budgeted up front, latency-critical loops).  Its output must equal the
+context-based sp_detect on the same sketch, bit for bit, call after call:
+the scratch array it shares across calls keeps the previous contents, so a
+stale status or a wrong estimate table would show up on a later call.
 
 This file is collected last so that a failure here leaves every other test
 already run."""
@@ -32,12 +32,12 @@ def torch():
     return t
 
 
-def _sketch_and_reference(sp, torch, seed, n_planted, threshold):
+def _sketch_and_reference(sp, torch, seed, n_planted, threshold, **kw):
     """A sketch built through a context, its sp_detect output, and device
     copies of its SEAV/LDCA in the exported layout."""
     pairs, planted = W.single_window(seed=seed, n=1 << 18, n_background=16384, n_planted=n_planted,
                                      planted_degree=2500)
-    params = sp.make_params(seed=seed)
+    params = sp.make_params(seed=seed, **kw)
     with sp.SuperPoint(params) as ctx:
         flat = torch.from_numpy(pairs.reshape(-1).view(np.int32).copy()).cuda()
         ctx.update(flat)
@@ -91,3 +91,16 @@ def test_noalloc_limits_and_overflow(sp, torch):
     rc, count, flags, recs = _noalloc(sp, torch, params, dseav, dldca, 0, 4)
     assert rc == sp.SP_OK and count == n and flags & 1 and len(recs) == 4
     assert set(recs["ip"].tolist()) <= set(want["ip"].tolist())
+
+
+def test_noalloc_estimate_table_of_each_k(sp, torch):
+    """The estimate tables of every supported k live side by side in the
+    shared array; calls with k = 256, 4096 and 1024 in a row each read their
+    own table (the est bits are compared, so a wrong table offset fails)."""
+    cases = [dict(k_log2=8, lc_log2=16), dict(k_log2=12, lc_log2=14), dict()]
+    for i, kw in enumerate(cases):
+        params, dseav, dldca, want, n = _sketch_and_reference(sp, torch, seed=31 + i, n_planted=6,
+                                                              threshold=1024, **kw)
+        rc, count, flags, recs = _noalloc(sp, torch, params, dseav, dldca, 1024, sp.SP_NOALLOC_MAX_RESULTS)
+        assert rc == sp.SP_OK and flags == 0 and count == n, kw
+        _same(recs, want)
