@@ -154,8 +154,11 @@ struct sp_ctx {
 // detection of this kind is in the paper: it keeps a host thread from
 // waiting forever on a stream that stopped making progress.
 static int wait_event_bounded(const sp_ctx* ctx, cudaEvent_t ev) {
+  // the first 20 ms poll with yields only (a sleep can last far longer than
+  // asked for, which would add to every detect's latency); longer waits
+  // sleep between polls
   const auto t0 = std::chrono::steady_clock::now();
-  for (uint32_t polls = 0;; ++polls) {
+  for (;;) {
     const cudaError_t q = cudaEventQuery(ev);
     if (q == cudaSuccess) return SP_OK;
     if (q != cudaErrorNotReady) {
@@ -163,12 +166,10 @@ static int wait_event_bounded(const sp_ctx* ctx, cudaEvent_t ev) {
       return SP_ERR_CUDA;
     }
     if (cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();   // not an error: keep launches' checks clean
-    if (ctx->timeout_ms) {
-      const auto waited = std::chrono::steady_clock::now() - t0;
-      if (waited >= std::chrono::milliseconds(ctx->timeout_ms)) return SP_ERR_TIMEOUT;
-    }
-    if (polls < 256) std::this_thread::yield();
-    else std::this_thread::sleep_for(std::chrono::microseconds(20));
+    const auto waited = std::chrono::steady_clock::now() - t0;
+    if (ctx->timeout_ms && waited >= std::chrono::milliseconds(ctx->timeout_ms)) return SP_ERR_TIMEOUT;
+    if (waited < std::chrono::milliseconds(20)) std::this_thread::yield();
+    else std::this_thread::sleep_for(std::chrono::microseconds(100));
   }
 }
 

@@ -83,14 +83,21 @@ def _distinct_peers(rng, d: int) -> np.ndarray:
     return rng.permutation(peers)[:d]
 
 
+def _rows(pairs: np.ndarray, idx: np.ndarray) -> np.ndarray:
+    """pairs[idx] for an (n, 2) uint32 array, gathered as 64-bit rows (the
+    same values as 2-D fancy indexing, about three times faster)."""
+    flat = np.ascontiguousarray(pairs, np.uint32).view(np.uint64).reshape(-1)
+    return flat[idx].view(np.uint32).reshape(-1, 2)
+
+
 def _fit_to(rng, pairs: np.ndarray, n: int) -> np.ndarray:
     """Shuffle, then truncate to n pairs or pad with duplicates of emitted pairs."""
-    pairs = pairs[rng.permutation(pairs.shape[0])]
+    pairs = _rows(pairs, rng.permutation(pairs.shape[0]))
     if pairs.shape[0] >= n:
         return np.ascontiguousarray(pairs[:n])
-    extra = pairs[rng.integers(0, pairs.shape[0], n - pairs.shape[0])]
+    extra = _rows(pairs, rng.integers(0, pairs.shape[0], n - pairs.shape[0]))
     out = np.concatenate([pairs, extra])
-    return np.ascontiguousarray(out[rng.permutation(n)])
+    return _rows(out, rng.permutation(n))
 
 
 def single_window(seed: int = 1, n: int = 1 << 20, n_background: int = 65536,
@@ -132,15 +139,15 @@ def core_link(seed: int = 2, n: int = 1 << 26, n_sources: int | None = None,
     sources = _distinct_hosts(rng, n_sources)
     planted = _distinct_hosts(rng, n_planted, exclude=sources)
     bg = _expand(rng, sources, _zipf_degrees(rng, n_sources, 1.1, cap_lo))
-    bg = bg[rng.permutation(bg.shape[0])][: max(0, n_distinct - int(planted_deg.sum()))]
+    bg = _rows(bg, rng.permutation(bg.shape[0]))[: max(0, n_distinct - int(planted_deg.sum()))]
     sp = np.concatenate([
         np.stack([np.full(d, h, np.uint32), _distinct_peers(rng, int(d))], 1)
         for h, d in zip(planted, planted_deg)
     ])
     distinct = np.concatenate([bg, sp])
-    dups = distinct[rng.integers(0, distinct.shape[0], n - distinct.shape[0])]
+    dups = _rows(distinct, rng.integers(0, distinct.shape[0], n - distinct.shape[0]))
     pairs = np.concatenate([distinct, dups])
-    pairs = np.ascontiguousarray(pairs[rng.permutation(pairs.shape[0])])
+    pairs = _rows(pairs, rng.permutation(pairs.shape[0]))
     return pairs, np.sort(planted)
 
 
@@ -231,5 +238,5 @@ def sliding_stream(seed: int = 4, sizes: np.ndarray | None = None, n_sp: int = 6
         bg = np.stack([hosts[rng.integers(0, hosts.size, room)],
                        rng.integers(0, 2**32, room, dtype=np.uint32)], 1)
         both = np.concatenate([bg, sp])
-        slices.append(np.ascontiguousarray(both[rng.permutation(both.shape[0])]))
+        slices.append(_rows(both, rng.permutation(both.shape[0])))
     return slices, sp_hosts, schedule
