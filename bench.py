@@ -278,7 +278,8 @@ def run_ours(args):
     from paper_1901_07306_gb300 import exchange
     total_ms = exchange.reduce_max(total_ms)
     recs, n_found, rc = sp.sp_results(c)
-    found = set(recs["ip"].tolist())
+    found_ips = recs["ip"].copy()
+    found = set(found_ips.tolist())
     recall = len(found & set(planted.tolist())) / len(planted)
 
     # end to end through the public API: pinned host pairs -> sp_update_host
@@ -371,6 +372,13 @@ def run_ours(args):
 
     sp.sp_destroy(c)
     ctx.ctx = None
+    acc = accuracy(found_ips, exact_super_points(pairs, theta)) if not args.no_extra else None
+    # the batched and served forms, each timed on its own after the headline region
+    legs = None
+    if rank == 0 and world == 1 and not args.no_extra:
+        legs = {"distributed": distributed_leg(torch, sp, W, 24, 64, steps=5, warmup=3),
+                "sliding": sliding_leg(torch, sp, W, 28, passes=1, warmup=1),
+                "serving": serving_leg(torch, sp, W, requests=400, runs=3, warmup=1)}
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -397,11 +405,13 @@ def run_ours(args):
         "detect_latency_ms": {"p50": det_sorted[len(det_sorted) // 2],
                               "p99": det_sorted[min(len(det_sorted) - 1, int(0.99 * len(det_sorted)))]},
         "super_points": {"found": int(n_found), "planted_recall": recall},
+        "accuracy": acc,
         "clocks": clk,
         "gpu_launches": launches_per_step(n, args.scan_mode) * K,
         "cpu_baseline": cpu,
         "cpu_baseline_threads": cpu_threads,
         "e2e": e2e,
+        "workloads": legs,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -409,11 +419,31 @@ def run_ours(args):
     return 0
 
 
-# ---- the other workloads (printed as their own JSON lines) ----------------
+# ---- the other workloads ----------------------------------------------------
+# Each leg returns a dict; ``--workload X`` prints it as its own JSON line and
+# the default core-link run embeds a compact form of every leg under
+# "workloads" (timed after, and outside, the headline region).
 D3 = dict(r=16, isb=(0, 4, 8, 12), ibn=(7, 7, 7, 7), lc_log2=18)   # 16 routers x 2^24 pairs merged
 # serving windows of 2^24 pairs: a quarter of profile D's SEAs and LDCs keeps
 # its load per SE and per LDC (SEAV 2 MiB + LDCA 8 MiB per router)
 PROFILE_S = dict(r=12, isb=(0, 5, 10, 15), ibn=(7, 7, 7, 7), lc_log2=14)
+
+
+def exact_super_points(pairs, theta):
+    """Ground truth of Def. 1-2 (not the method): the hosts with at least
+    theta distinct opposite IPs, by sort-unique of the distinct pairs."""
+    keys = np.unique(np.ascontiguousarray(pairs, np.uint32).view(np.uint64).reshape(-1))
+    hosts, counts = np.unique((keys & np.uint64(0xFFFFFFFF)).astype(np.uint32), return_counts=True)
+    return hosts[counts >= theta]
+
+
+def accuracy(found, truth):
+    """Sec. 6: FPR = detected hosts that are not super points / super points,
+    FNR = super points not detected / super points, FTR = FPR + FNR."""
+    found, truth = set(np.asarray(found).tolist()), set(np.asarray(truth).tolist())
+    n = max(1, len(truth))
+    fpr, fnr = len(found - truth) / n, len(truth - found) / n
+    return {"super_points": len(truth), "detected": len(found), "fpr": fpr, "fnr": fnr, "ftr": fpr + fnr}
 
 
 def _device_setup():
@@ -428,6 +458,11 @@ def _device_setup():
 def _gpu_index():
     v = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     return int(v.split(",")[0]) if v.split(",")[0].isdigit() else 0
+
+
+def _pcts(xs):
+    s = sorted(xs)
+    return {"p50": s[len(s) // 2], "p99": s[min(len(s) - 1, int(0.99 * len(s)))]}
 
 
 def _timed(torch, fn, steps, warmup, clocks=None):
@@ -445,23 +480,22 @@ def _timed(torch, fn, steps, warmup, clocks=None):
     return a.elapsed_time(b) / steps
 
 
-def run_distributed(args):
-    """16 simulated border routers, each 2^24 pairs arriving as uneven time-slice
-    batches; one step = reset, scan every batch, OR-merge into the global
-    router, detect.  Batched (one sp_update_batched call) vs one launch per
-    batch (sp_update per batch)."""
-    torch, sp, W = _device_setup()
-    n_routers, per = 16, 1 << args.router_log2
+def distributed_leg(torch, sp, W, router_log2=24, batches_per_router=64, steps=10, warmup=3, with_accuracy=False):
+    """16 simulated border routers, each 2^router_log2 pairs arriving as
+    uneven time-slice batches; one step = reset, scan every batch, OR-merge
+    into the global router, detect.  Batched (one sp_update_batched call) vs
+    one launch per batch (sp_update per batch)."""
+    n_routers, per = 16, 1 << router_log2
     routers, sp_hosts = W.distributed(seed=3, n_per_router=per)
     rng = np.random.default_rng(3)
+    flats = [torch.from_numpy(pr.reshape(-1).view(np.int32)).cuda() for pr in routers]
     batches = []
     for r, pr in enumerate(routers):
-        w = np.exp(rng.uniform(0, np.log(16.0), args.batches_per_router))
+        w = np.exp(rng.uniform(0, np.log(16.0), batches_per_router))
         cuts = np.floor(np.cumsum(w / w.sum())[:-1] * pr.shape[0]).astype(np.int64)
-        for part in np.split(pr, cuts):
-            batches.append((r, torch.from_numpy(np.ascontiguousarray(part).reshape(-1).view(np.int32)).cuda()))
-    order = rng.permutation(len(batches))
-    batches = [batches[i] for i in order]
+        bounds = [0, *cuts.tolist(), pr.shape[0]]
+        batches += [(r, flats[r][2 * a:2 * b]) for a, b in zip(bounds[:-1], bounds[1:])]
+    batches = [batches[i] for i in rng.permutation(len(batches))]
     total = sum(t.numel() // 2 for _, t in batches)
     stream = torch.cuda.current_stream()
     ctx = sp.SuperPoint(sp.make_params(theta=1024, seed=3, n_routers=n_routers + 1, **D3), stream=stream)
@@ -480,35 +514,34 @@ def run_distributed(args):
         sp.sp_detect_async(c, n_routers, 1024)
 
     clocks = ClockSampler(_gpu_index())
-    ms_b = _timed(torch, lambda: step(True), args.steps, args.warmup, clocks)
+    ms_b = _timed(torch, lambda: step(True), steps, warmup, clocks)
     clk = clocks.stop()
     res_b, n_b, _ = sp.sp_results(c)
-    ms_p = _timed(torch, lambda: step(False), max(3, args.steps // 4), 3)
+    ms_p = _timed(torch, lambda: step(False), max(3, steps // 2), 3)
     res_p, n_p, _ = sp.sp_results(c)
-    assert np.array_equal(res_b, res_p), "batched and per-batch paths disagree"
-    recall = len(set(res_b["ip"].tolist()) & set(sp_hosts.tolist())) / len(sp_hosts)
-    line = {"metric": METRIC, "value": total / (ms_b * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"distributed: {n_routers} routers x 2^{args.router_log2} pairs from an overlapping "
-                                   "host population, 1,000 global super points split across routers, "
-                                   f"{args.batches_per_router} uneven batches per router; reset + scan + OR-merge + "
-                                   "detect per step; profile D3 (r=16, LC=2^18)",
-                       "n_pairs": total, "batches": len(batches)},
-            "plain_per_batch": {"value": total / (ms_p * 1e-3), "ms_per_step": ms_p},
-            "batched_speedup": ms_p / ms_b,
-            "super_points": {"found": int(n_b), "global_recall": recall}, "clocks": clk}
     ctx.close()
-    print(json.dumps(line), flush=True)
-    return 0
+    assert np.array_equal(res_b, res_p), "batched and per-batch paths disagree"
+    out = {"workload": f"distributed: {n_routers} routers x 2^{router_log2} pairs from an overlapping host population, "
+                       f"1,000 global super points split across routers, {batches_per_router} uneven batches per "
+                       "router; reset + scan + OR-merge + detect per step; profile D3 (r=16, LC=2^18)",
+           "n_pairs": total, "batches": len(batches), "steps": steps,
+           "batched": {"value": total / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b},
+           "plain_per_batch": {"value": total / (ms_p * 1e-3), "unit": UNIT, "ms_per_step": ms_p},
+           "batched_speedup": ms_p / ms_b,
+           "super_points": {"found": int(n_b),
+                            "global_recall": len(set(res_b["ip"].tolist()) & set(sp_hosts.tolist())) / len(sp_hosts)},
+           "clocks": clk}
+    if with_accuracy:
+        out["accuracy"] = accuracy(res_b["ip"], exact_super_points(np.concatenate(routers), 1024))
+    return out
 
 
-def run_sliding(args):
+def sliding_leg(torch, sp, W, total_log2=28, passes=2, warmup=1, checkpoints=()):
     """A stream of time slices of lognormal size (2^28 pairs in 128 slices at
     full size), window of 32 slices advanced one slice at a time (Sec. 5):
-    per slice = slide + scan the slice + detect the window."""
-    torch, sp, W = _device_setup()
-    T = args.slide_total_log2
+    per slice = slide + scan the slice + detect the window.  checkpoints:
+    slices whose window's detection is scored against exact ground truth."""
+    T = total_log2
     scale = 1 << max(0, 28 - T)
     sizes = W.slice_sizes(4, n_slices=128, total=1 << T, lo=(1 << 19) // scale, hi=(1 << 22) // scale)
     slices, sp_hosts, sched = W.sliding_stream(seed=4, sizes=sizes, n_sp=64, sp_degree_per_slice=(64, 512))
@@ -517,8 +550,9 @@ def run_sliding(args):
     k = 32
     ctx = sp.SuperPoint(sp.make_params(theta=1024, seed=4, window_slices=k), stream=stream)
     c = ctx.ctx
+    found = {}
 
-    def one_pass(record):
+    def one_pass(keep=()):
         sp.sp_reset(c, 0)
         evs = []
         for t, x in enumerate(dev_slices):
@@ -531,50 +565,50 @@ def run_sliding(args):
             sp.sp_detect_async(c, 0, 1024)
             e1.record(stream)
             evs.append((e0, e1))
+            if t in keep:
+                found[t] = sp.sp_results(c)[0]["ip"]
         return evs
 
-    for _ in range(max(3, args.warmup)):              # warm up: whole passes over the stream
-        one_pass(False)
+    for _ in range(max(1, warmup)):                   # warm up: whole passes over the stream
+        one_pass()
     torch.cuda.synchronize()
-    passes = max(1, min(args.steps, 5))
     clocks = ClockSampler(_gpu_index())
     clocks.start()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     evs = []
     for _ in range(passes):
-        evs += one_pass(True)
+        evs += one_pass()
     b.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = a.elapsed_time(b) / passes
-    det = sorted(e0.elapsed_time(e1) for e0, e1 in evs)
-    res, n_found, _ = sp.sp_results(c)
+    det = [e0.elapsed_time(e1) for e0, e1 in evs]
+    n_found = sp.sp_results(c)[1]
     total = int(sizes.sum())
-    line = {"metric": METRIC, "value": total / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": passes,
-            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "clocks": clk,
-            "config": {"workload": f"sliding window: 2^{T} pairs in 128 lognormal slices "
-                                   f"[{int(sizes.min())}, {int(sizes.max())}] pairs, window {k} slices advanced one "
-                                   "slice at a time; per slice slide + scan + detect; profile D with slice stamps; "
-                                   "one step = one pass over the stream",
-                       "n_pairs": total, "slices": len(slices), "window_slices": k,
-                       "l2": "the 320 MiB counter pool and 2^{T}-pair stream are larger than L2"},
-            "detect_latency_ms": {"p50": det[len(det) // 2], "p99": det[min(len(det) - 1, int(0.99 * len(det)))]},
-            "super_points_last_window": int(n_found)}
+    out = {"workload": f"sliding window: 2^{T} pairs in 128 lognormal slices [{int(sizes.min())}, {int(sizes.max())}] "
+                       f"pairs, window {k} slices advanced one slice at a time; per slice slide + scan + detect; "
+                       "profile D with slice stamps; one step = one pass over the stream",
+           "n_pairs": total, "slices": len(slices), "window_slices": k, "passes": passes,
+           "value": total / (ms * 1e-3), "unit": UNIT, "ms_per_pass": ms,
+           "detect_latency_ms": _pcts(det), "super_points_last_window": int(n_found), "clocks": clk}
+    if checkpoints:
+        one_pass(keep=set(checkpoints))
+        out["accuracy"] = {str(t): accuracy(found[t], exact_super_points(
+            np.concatenate(slices[max(0, t - k + 1):t + 1]), 1024)) for t in sorted(found)}
     ctx.close()
-    print(json.dumps(line), flush=True)
-    return 0
+    return out
 
 
-def run_serving(args):
+def serving_leg(torch, sp, W, requests=400, runs=3, warmup=1, window_slices=1):
     """64 routers sending batches of 2^12-2^22 pairs (log-uniform) with Poisson
     arrivals; continuous batching under a 2 GiB staging budget vs the plain
-    one-launch-per-batch path, a detect every 2^24 global pairs."""
-    torch, sp, W = _device_setup()
+    one-launch-per-batch path, a detect every 2^24 global pairs.  Throughput
+    with the offered load above capacity (median of the runs), then
+    batch-to-result latency at half the plain path's capacity."""
     from paper_1901_07306_gb300 import serving as S
     n_routers = 64
-    reqs = S.poisson_requests(5, n_routers, args.requests, rate_pairs_per_s=1e13, lo_log2=12, hi_log2=22)
+    reqs = S.poisson_requests(5, n_routers, requests, rate_pairs_per_s=1e13, lo_log2=12, hi_log2=22)
     total = sum(r.n_pairs for r in reqs)
 
     def serve(batched, rate):
@@ -584,16 +618,15 @@ def run_serving(args):
         arr = np.cumsum(gaps) - gaps[0]
         rs = [S.Request(router=r.router, pairs=r.pairs, arrival=float(a)) for r, a in zip(reqs, arr)]
         srv = S.SketchServer(n_routers, dict(PROFILE_S, theta=1024, seed=5), budget_bytes=2 << 30,
-                             detect_every=1 << 24, window_slices=args.serve_window_slices, batched=batched)
+                             detect_every=1 << 24, window_slices=window_slices, batched=batched)
         try:
             wins = srv.run(rs)
         finally:
             srv.close()
         return rs, wins, srv.elapsed
 
-    for _ in range(max(3, args.warmup)):                             # warm up (allocations, build)
+    for _ in range(max(1, warmup)):                                   # warm up (allocations, build)
         serve(True, 1e13)
-    runs = max(3, min(args.steps, 5))
     clocks = ClockSampler(_gpu_index())
     clocks.start()
     # offered load above capacity; host-driven, so the median of several runs
@@ -606,21 +639,49 @@ def run_serving(args):
     rate = 0.5 * total / tp                                          # half the plain path's capacity
     lb, _, _ = serve(True, rate)
     lp, _, _ = serve(False, rate)
-    line = {"metric": METRIC, "value": total / tb, "unit": UNIT, "n_gpus": 1, "steps": runs,
-            "warmup": max(3, args.warmup), "ms_per_step": tb * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "clocks": clk,
+    return {"workload": f"serving: {n_routers} routers, {len(reqs)} batches of 2^12-2^22 pairs (log-uniform), Poisson "
+                        "arrivals, 2 GiB staging budget, detect every 2^24 global pairs (OR-merge into a global "
+                        "router), profile S (r=12, LC=2^14), "
+                        + (f"sliding window of {window_slices} detect periods" if window_slices > 1
+                           else "discrete windows") + "; value = median of the runs (host wall clock)",
+            "n_pairs": total, "windows": len(wb), "runs": runs,
             "runs_ms": {"batched": [round(x[2] * 1e3, 3) for x in bat], "plain": [round(x[2] * 1e3, 3) for x in pla]},
-            "config": {"workload": f"serving: {n_routers} routers, {len(reqs)} batches of 2^12-2^22 pairs "
-                                   "(log-uniform), Poisson arrivals, 2 GiB staging budget, detect every 2^24 "
-                                   "global pairs (OR-merge into a global router), profile S (r=12, LC=2^14), "
-                                   + (f"sliding window of {args.serve_window_slices} detect periods"
-                                      if args.serve_window_slices > 1 else "discrete windows")
-                                   + "; value = median of the runs (host wall clock)",
-                       "n_pairs": total, "windows": len(wb)},
-            "plain_per_batch": {"value": total / tp, "ms": tp * 1e3},
+            "batched": {"value": total / tb, "unit": UNIT, "ms": tb * 1e3},
+            "plain_per_batch": {"value": total / tp, "unit": UNIT, "ms": tp * 1e3},
+            "batched_speedup": tp / tb,
             "latency_at_half_plain_capacity": {"offered_pairs_per_s": rate, "batched": S.latency_summary(lb),
-                                               "plain": S.latency_summary(lp)}}
-    print(json.dumps(line), flush=True)
+                                               "plain": S.latency_summary(lp)},
+            "clocks": clk}
+
+
+def _line(leg, args, value, ms):
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": leg.pop("workload"), "n_pairs": leg["n_pairs"]},
+            "clocks": leg.pop("clocks"), **leg}
+
+
+def run_distributed(args):
+    torch, sp, W = _device_setup()
+    leg = distributed_leg(torch, sp, W, args.router_log2, args.batches_per_router, args.steps, args.warmup,
+                          with_accuracy=True)
+    print(json.dumps(_line(leg, args, leg["batched"]["value"], leg["batched"]["ms_per_step"])), flush=True)
+    return 0
+
+
+def run_sliding(args):
+    torch, sp, W = _device_setup()
+    leg = sliding_leg(torch, sp, W, args.slide_total_log2, max(1, min(args.steps, 5)), args.warmup,
+                      checkpoints=(31, 64, 127))
+    print(json.dumps(_line(leg, args, leg["value"], leg["ms_per_pass"])), flush=True)
+    return 0
+
+
+def run_serving(args):
+    torch, sp, W = _device_setup()
+    leg = serving_leg(torch, sp, W, args.requests, max(3, min(args.steps, 5)), args.warmup,
+                      args.serve_window_slices)
+    print(json.dumps(_line(leg, args, leg["batched"]["value"], leg["batched"]["ms"])), flush=True)
     return 0
 
 
@@ -633,6 +694,8 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the accuracy report and the distributed, sliding and serving legs")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-budget", type=float, default=60.0)

@@ -274,6 +274,27 @@ SP_API int sp_autotune(sp_ctx* ctx, const uint32_t* dev_pairs, uint64_t n_pairs,
  * Errors: SP_ERR_ROUTER, SP_ERR_PARAM, SP_ERR_STATE. */
 SP_API int sp_merge(sp_ctx* ctx, const uint32_t* routers, uint32_t n, uint32_t dst_router);
 
+/* Device image of one router for a WP -> GS shipment that stays in device
+ * memory (Sec. 4.2 over NCCL or another device transport): copies the
+ * router's sketch to dev_dst (device memory, 16-byte aligned) on the stream,
+ * in the context's device layout -- the SEAV bytes [2^r][sum SC(i)], zero
+ * padding to a multiple of 256 bytes, the LDCA words [lr][LC][k / 32], zero
+ * padding to a multiple of 256 bytes -- which is the same for every context
+ * with the same parameters.  Pending binned-scan planes are folded first; a
+ * sliding context copies the bits of its current window.  With dev_dst NULL
+ * *n receives the image size.  Async.  Errors: SP_ERR_TRUNCATED (cap too
+ * small), SP_ERR_ROUTER, SP_ERR_PARAM (misaligned dev_dst), SP_ERR_CUDA. */
+SP_API int sp_copy_sketch(sp_ctx* ctx, uint32_t router, void* dev_dst, uint64_t cap, uint64_t* n);
+
+/* Global SEAV/LDCA of Sec. 4.2 from images in device memory: dst |= every
+ * image of dev_images[0 .. n) (a host array of device pointers, each image
+ * 16-byte aligned, written by sp_copy_sketch of a context with the same
+ * parameters -- e.g. gathered from other GPUs), bitwise OR over the whole
+ * image on the GPU.  The images are read when the stream reaches the merge.
+ * Async.  Discrete contexts only (SP_ERR_STATE in a sliding context).
+ * Errors: SP_ERR_ROUTER, SP_ERR_PARAM (NULL or misaligned image), SP_ERR_CUDA. */
+SP_API int sp_merge_device(sp_ctx* ctx, const void* const* dev_images, uint32_t n, uint32_t dst_router);
+
 /* Restore + filter (Sec. 3.2-3.3) on one router's sketch, enqueued on the
  * stream: HSE(i) = SEs of weight >= 3; every candidate index set of the
  * cartesian product whose rows agree on their shared LP bits and whose SEU

@@ -858,6 +858,35 @@ int sp_merge(sp_ctx* ctx, const uint32_t* routers, uint32_t n, uint32_t dst_rout
              ? SP_OK : SP_ERR_CUDA;
 }
 
+int sp_copy_sketch(sp_ctx* ctx, uint32_t router, void* dev_dst, uint64_t cap, uint64_t* n) {
+  if (!ctx || !n) return SP_ERR_PARAM;
+  if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
+  *n = ctx->stride;
+  if (!dev_dst) return SP_OK;
+  if (cap < ctx->stride) return SP_ERR_TRUNCATED;
+  if ((uintptr_t)dev_dst & 15u) return SP_ERR_PARAM;
+  int frc = ctx->sliding ? commit_window(ctx, router) : fold_router(ctx, router);
+  if (frc != SP_OK) return frc;
+  const uint8_t* src = ctx->sliding ? ctx->wseav(router) : ctx->seav(router);
+  return cudaMemcpyAsync(dev_dst, src, ctx->stride, cudaMemcpyDeviceToDevice, ctx->stream) == cudaSuccess
+             ? SP_OK : SP_ERR_CUDA;
+}
+
+int sp_merge_device(sp_ctx* ctx, const void* const* dev_images, uint32_t n, uint32_t dst_router) {
+  if (!ctx || (n && !dev_images)) return SP_ERR_PARAM;
+  if (dst_router >= ctx->p.n_routers) return SP_ERR_ROUTER;
+  if (ctx->sliding) return SP_ERR_STATE;      // an image holds window bits, not slice stamps
+  std::vector<const uint8_t*> srcs(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    if (!dev_images[i] || ((uintptr_t)dev_images[i] & 15u)) return SP_ERR_PARAM;
+    srcs[i] = static_cast<const uint8_t*>(dev_images[i]);
+  }
+  const int rc = fold_router(ctx, dst_router);
+  if (rc != SP_OK) return rc;
+  return sp::launch_merge(ctx->seav(dst_router), srcs.data(), n, ctx->stride, ctx->stream) == cudaSuccess
+             ? SP_OK : SP_ERR_CUDA;
+}
+
 int sp_detect_async(sp_ctx* ctx, uint32_t router, uint32_t threshold) {
   if (!ctx) return SP_ERR_PARAM;
   if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;

@@ -345,7 +345,15 @@ k_apply(DevParams d, const uint32_t* __restrict__ lists, const uint32_t* __restr
 #pragma unroll
       for (int u = 0; u < kApplyUnroll; ++u) set_bits(hip[u]);
     }
-    for (uint32_t i = i0 + lane; i < n; i += 32) set_bits(__ldcs(src - lane + i));
+    if (i0 < n) {                                   // the last, partial round: masked, loads still in flight together
+      uint32_t hip[kApplyUnroll];
+#pragma unroll
+      for (int u = 0; u < kApplyUnroll; ++u)
+        hip[u] = (i0 + u * 32 + lane < n) ? __ldcs(src + i0 + u * 32) : 0u;
+#pragma unroll
+      for (int u = 0; u < kApplyUnroll; ++u)
+        if (i0 + u * 32 + lane < n) set_bits(hip[u]);
+    }
   }
   __syncthreads();
   for (uint32_t w = tid; w < words; w += kApplyThreads) *at_word(w) = s_plane[w];

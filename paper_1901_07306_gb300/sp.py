@@ -41,7 +41,7 @@ EXPORTED = (
     "sp_reset", "sp_update", "sp_update_host", "sp_update_batched", "sp_merge",
     "sp_detect_async", "sp_results", "sp_detect", "sp_results_device", "sp_slide",
     "sp_export", "sp_import", "sp_detect_noalloc", "sp_update_batched_device", "sp_autotune",
-    "sp_results_async", "sp_psu", "sp_size_ldca", "sp_set_timeout",
+    "sp_results_async", "sp_psu", "sp_size_ldca", "sp_set_timeout", "sp_copy_sketch", "sp_merge_device",
 )
 
 
@@ -100,6 +100,8 @@ def _load():
         "sp_update_host": (i32, [vp, u32, vp, u64]),
         "sp_update_batched": (i32, [vp, u32, P(u32), P(vp), P(u64)]),
         "sp_merge": (i32, [vp, P(u32), u32, u32]),
+        "sp_copy_sketch": (i32, [vp, u32, vp, u64, P(u64)]),
+        "sp_merge_device": (i32, [vp, P(vp), u32, u32]),
         "sp_detect_async": (i32, [vp, u32, u32]),
         "sp_results": (i32, [vp, vp, u64, P(u64)]),
         "sp_detect": (i32, [vp, u32, u32, vp, u64, P(u64)]),
@@ -275,6 +277,26 @@ def sp_autotune(ctx: int, dev_pairs):
 def sp_merge(ctx: int, routers, dst_router: int) -> None:
     arr = (ctypes.c_uint32 * len(routers))(*routers)
     _check(lib.sp_merge(ctypes.c_void_p(ctx), arr, len(routers), dst_router), "sp_merge")
+
+
+def sp_copy_sketch_bytes(ctx: int) -> int:
+    n = ctypes.c_uint64()
+    _check(lib.sp_copy_sketch(ctypes.c_void_p(ctx), 0, None, 0, ctypes.byref(n)), "sp_copy_sketch")
+    return n.value
+
+
+def sp_copy_sketch(ctx: int, router: int, dev_dst) -> None:
+    """dev_dst: CUDA uint8 tensor of at least sp_copy_sketch_bytes(ctx) bytes."""
+    n = ctypes.c_uint64()
+    _check(lib.sp_copy_sketch(ctypes.c_void_p(ctx), router, ctypes.c_void_p(dev_dst.data_ptr()),
+                              dev_dst.numel() * dev_dst.element_size(), ctypes.byref(n)), "sp_copy_sketch")
+
+
+def sp_merge_device(ctx: int, dev_images, dst_router: int) -> None:
+    """dev_images: CUDA tensors (or raw device addresses) of sp_copy_sketch images."""
+    ptrs = [x.data_ptr() if hasattr(x, "data_ptr") else int(x) for x in dev_images]
+    arr = (ctypes.c_void_p * max(1, len(ptrs)))(*ptrs)
+    _check(lib.sp_merge_device(ctypes.c_void_p(ctx), arr, len(ptrs), dst_router), "sp_merge_device")
 
 
 def sp_detect_async(ctx: int, router: int = 0, threshold: int = 0) -> int:

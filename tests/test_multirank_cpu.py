@@ -1,6 +1,8 @@
 """World-size-2 gloo tests of the multi-process host logic (CPU only): the
 max-over-ranks timing of the benchmark and the all-gather of exported sketch
-images used for the cross-box OR-merge of Sec. 4.2."""
+images used for the cross-box OR-merge of Sec. 4.2 (equal sizes on every
+rank, a mismatch reported on every rank), and a rank that dies before the
+exchange."""
 import os
 import socket
 
@@ -22,8 +24,13 @@ def _worker(rank, world, port, q):
     try:
         from paper_1901_07306_gb300 import exchange
         t = exchange.reduce_max(10.0 * (rank + 1))
-        imgs = exchange.all_gather_images(bytes([rank]) * (1000 + rank))
-        q.put((rank, t, [len(x) for x in imgs], [x[:1] for x in imgs]))
+        imgs = exchange.all_gather_images(bytes([rank, 7]) * 500)
+        try:
+            exchange.all_gather_images(bytes([rank]) * (1000 + rank))
+            mismatch = "no error"
+        except ValueError:
+            mismatch = "ValueError"
+        q.put((rank, t, [len(x) for x in imgs], [x[:2] for x in imgs], mismatch))
     finally:
         dist.destroy_process_group()
 
@@ -56,9 +63,10 @@ def test_reduce_max_and_gather_images():
         p.join(timeout=60)
         assert p.exitcode == 0
     for r in range(2):
-        t, lens, heads = out[r]
+        t, lens, heads, mismatch = out[r]
         assert t == 20.0
-        assert lens == [1000, 1001] and heads == [b"\x00", b"\x01"]
+        assert lens == [1000, 1000] and heads == [b"\x00\x07", b"\x01\x07"]
+        assert mismatch == "ValueError"
 
 
 def test_dead_rank_surfaces_as_error():
