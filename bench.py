@@ -7,9 +7,14 @@ device).  Inputs are resident in HBM when the timed region starts and are
 larger than L2 (512 MiB of pairs vs 129 MB).
 
 Prints ONE JSON line on rank 0 (see the keys below).  N > 1 runs under
-torchrun as independent watch points, one per GPU (weak scaling: each rank
-scans its own window; no collective in the data path, only the barrier and
-the max-over-ranks timing).
+torchrun as watch points, one per GPU (weak scaling: each rank scans its own
+window in the headline region, whose only collectives are the barrier and the
+max-over-ranks timing); after it, the WP -> GS exchange of Sec. 4.2 (NCCL
+all-gather of the device sketches, OR on the GPU, detect) is timed and
+checked bit-exact against one GPU's scan of the union stream ("exchange").
+At N = 1 the line also carries the accuracy of the window against exact
+ground truth (Sec. 6 FPR/FNR) and the distributed, sliding-window and
+serving workloads ("workloads"), each timed on its own after the headline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -236,9 +241,12 @@ def run_ours(args):
     flat = torch.from_numpy(pairs.reshape(-1).view(np.int32))
     dev_pairs = flat.cuda()
     stream = torch.cuda.current_stream()
-    params = sp.make_params(seed=seed, theta=theta, scan_mode=args.scan_mode)
+    # router 1 is the global server of the multi-GPU exchange
+    params = sp.make_params(seed=args.seed, theta=theta, scan_mode=args.scan_mode, n_routers=2 if world > 1 else 1)
     ctx = sp.SuperPoint(params, stream=stream)
     c = ctx.ctx
+    # the binned scan's staging shape, tuned on a sample of the window
+    shape = sp.sp_autotune_binned(c, dev_pairs[: 2 << 24]) if args.scan_mode != 1 else None
 
     def step():
         sp.sp_reset(c, 0)
@@ -370,6 +378,10 @@ def run_ours(args):
                        "sample": f"the whole 2^26-pair window in {thr} shards, then the merge and one detect, "
                                  f"{dt_mt:.1f} s"}
 
+    # N > 1: the WP -> GS exchange (Sec. 4.2) over NCCL, timed after the
+    # headline region: every rank's device sketch all-gathered, ORed into a
+    # global router and detected on every rank
+    xchg = exchange_leg(torch, sp, W, c, args, rank, world) if world > 1 else None
     sp.sp_destroy(c)
     ctx.ctx = None
     acc = accuracy(found_ips, exact_super_points(pairs, theta)) if not args.no_extra else None
@@ -394,6 +406,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD if args.pairs_log2 == 26 else f"{WORKLOAD} [scaled to 2^{args.pairs_log2} pairs]",
                    "n_pairs": n, "threshold": theta, "profile": "D", "scan_mode": args.scan_mode,
+                   "binned_shape": shape,
                    "l2": "inputs larger than L2 (512 MiB of pairs per step vs 129 MB L2)",
                    "parallelism": f"{world} independent watch point(s), one per GPU"},
         "roofline": {"kernel": ("scan stage k_bin + k_apply (binned)" if args.scan_mode != 1 else "k_scan (direct)"),
@@ -412,6 +425,7 @@ def run_ours(args):
         "cpu_baseline_threads": cpu_threads,
         "e2e": e2e,
         "workloads": legs,
+        "exchange": xchg,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -427,6 +441,57 @@ D3 = dict(r=16, isb=(0, 4, 8, 12), ibn=(7, 7, 7, 7), lc_log2=18)   # 16 routers 
 # serving windows of 2^24 pairs: a quarter of profile D's SEAs and LDCs keeps
 # its load per SE and per LDC (SEAV 2 MiB + LDCA 8 MiB per router)
 PROFILE_S = dict(r=12, isb=(0, 5, 10, 15), ibn=(7, 7, 7, 7), lc_log2=14)
+
+
+def exchange_leg(torch, sp, W, c, args, rank, world, steps=10):
+    """Multi-GPU WP -> GS exchange (Sec. 4.2), NCCL device form: time of
+    all-gather of the ranks' device sketches + OR into router 1 + detect (max
+    over ranks), and a bit-exactness check of the same path on 2^22-pair
+    windows against one GPU's scan of the ranks' concatenated streams (rank 0;
+    the OR of the sketches equals the sketch of the union stream)."""
+    from paper_1901_07306_gb300 import exchange
+    theta = 1024
+
+    def gather_merge_detect(ctx_):
+        g = exchange.all_gather_sketches(sp, ctx_, 0)
+        sp.sp_reset(ctx_, 1)
+        exchange.merge_gathered(sp, ctx_, g, 1)
+        sp.sp_detect_async(ctx_, 1, theta)
+        return g
+
+    for _ in range(3):
+        gather_merge_detect(c)
+    torch.cuda.synchronize()
+    torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        g = gather_merge_detect(c)
+    torch.cuda.synchronize()
+    ms = exchange.reduce_max(1e3 * (time.perf_counter() - t0) / steps)
+    n_found = sp.sp_results(c)[1]
+    # the check on small windows: every rank scans its own, the merged result
+    # must equal one scan of all ranks' windows
+    small = lambda r: W.core_link(seed=args.seed + r, n=1 << 22)[0]  # noqa: E731
+    stream = torch.cuda.current_stream()
+    chk = sp.SuperPoint(sp.make_params(seed=args.seed, theta=theta, n_routers=2), stream=stream)
+    sp.sp_update(chk.ctx, 0, torch.from_numpy(small(rank).reshape(-1).view(np.int32)).cuda())
+    gather_merge_detect(chk.ctx)
+    got = sp.sp_results(chk.ctx)[0]
+    merged_img = chk.sketch_image(1)
+    chk.close()
+    exact = None
+    if rank == 0:
+        one = sp.SuperPoint(sp.make_params(seed=args.seed, theta=theta), stream=stream)
+        for r in range(world):
+            sp.sp_update(one.ctx, 0, torch.from_numpy(small(r).reshape(-1).view(np.int32)).cuda())
+        want = one.detect()[0]
+        ref_img = one.sketch_image(0)
+        one.close()
+        exact = bool(np.array_equal(got, want) and all(np.array_equal(a, b) for a, b in zip(merged_img, ref_img)))
+        assert exact, "the exchanged global sketch differs from one scan of the union stream"
+    return {"form": "NCCL all-gather of device sketch images + OR on the GPU + detect",
+            "bytes_per_rank": int(g.shape[1]), "ms": ms, "global_super_points": int(n_found),
+            "bit_exact_vs_one_gpu_union_scan": exact, "check": f"{world} ranks x 2^22-pair windows"}
 
 
 def exact_super_points(pairs, theta):
@@ -500,6 +565,7 @@ def distributed_leg(torch, sp, W, router_log2=24, batches_per_router=64, steps=1
     stream = torch.cuda.current_stream()
     ctx = sp.SuperPoint(sp.make_params(theta=1024, seed=3, n_routers=n_routers + 1, **D3), stream=stream)
     c = ctx.ctx
+    shape = sp.sp_autotune_binned(c, flats[0])            # staging shape tuned on one router's stream
     rlist, tlist = [r for r, _ in batches], [t for _, t in batches]
 
     def step(batched):
@@ -524,7 +590,7 @@ def distributed_leg(torch, sp, W, router_log2=24, batches_per_router=64, steps=1
     out = {"workload": f"distributed: {n_routers} routers x 2^{router_log2} pairs from an overlapping host population, "
                        f"1,000 global super points split across routers, {batches_per_router} uneven batches per "
                        "router; reset + scan + OR-merge + detect per step; profile D3 (r=16, LC=2^18)",
-           "n_pairs": total, "batches": len(batches), "steps": steps,
+           "n_pairs": total, "batches": len(batches), "steps": steps, "binned_shape": shape,
            "batched": {"value": total / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b},
            "plain_per_batch": {"value": total / (ms_p * 1e-3), "unit": UNIT, "ms_per_step": ms_p},
            "batched_speedup": ms_p / ms_b,

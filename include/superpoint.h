@@ -265,6 +265,40 @@ SP_API int sp_update_batched_device(sp_ctx* ctx, const sp_batch* dev_batches, ui
 SP_API int sp_autotune(sp_ctx* ctx, const uint32_t* dev_pairs, uint64_t n_pairs,
                        uint32_t* best_threads, uint32_t* best_blocks);
 
+/* Staging shape of the binned scan (an implementation choice; the paper's
+ * per-pair update of Sec. 3.3 fixes only the bits, which every shape gives
+ * exactly): the binning block size, the hips a bin's shared-memory row
+ * holds, the tiles binned between two flushes of the rows to the lists, the
+ * binning blocks per SM, and the block size of the plane pass. */
+typedef struct sp_binned_shape {
+  uint32_t index;                /* position in the compiled list */
+  uint32_t bin_threads;
+  uint32_t bin_stage;
+  uint32_t bin_tiles_per_round;
+  uint32_t bin_blocks_per_sm;
+  uint32_t apply_threads;
+} sp_binned_shape;
+
+/* The compiled staging shapes: *n receives their number, out[0 .. min(cap, *n))
+ * their description (out may be NULL when cap = 0).  Shape 0 is the default. */
+SP_API int sp_binned_shapes(sp_binned_shape* out, uint32_t cap, uint32_t* n);
+
+/* Selects staging shape `index` for the context's later binned scans (results
+ * are identical for every shape).  Errors: SP_ERR_PARAM (index out of range). */
+SP_API int sp_set_binned_shape(sp_ctx* ctx, uint32_t index);
+
+/* The context's current staging shape. */
+SP_API int sp_get_binned_shape(const sp_ctx* ctx, sp_binned_shape* out);
+
+/* Autotuner of the binned scan: times every compiled staging shape on router
+ * 0 with the caller's sample stream dev_pairs[0 .. 2 n_pairs) (a binned scan
+ * of it, 3 times after a warm-up), keeps the fastest for this context and
+ * reports it in *best (may be NULL).  Router 0's sketch is reset afterwards.
+ * Synchronises the stream.  Errors: SP_ERR_PARAM (NULL, empty or misaligned
+ * sample), SP_ERR_STATE (the parameters rule the binned scan out: k > 1024,
+ * LC < 32 or lr * LC > 2^20), SP_ERR_NOMEM, SP_ERR_CUDA, SP_ERR_TIMEOUT. */
+SP_API int sp_autotune_binned(sp_ctx* ctx, const uint32_t* dev_pairs, uint64_t n_pairs, sp_binned_shape* best);
+
 /* Global SEAV/LDCA of Sec. 4.2: dst |= src for every source router, bitwise
  * OR over both structures (the OR of the WPs' sketches equals the sketch of
  * the union of their streams).  routers is a host array of n indices; it may

@@ -135,6 +135,7 @@ struct sp_ctx {
   uint32_t table_next = 0;
   int multi_threads = 256;
   int multi_grid = 0;
+  uint32_t bs_shape_index = 0;              // staging shape of the binned scan (sp_autotune_binned)
 
   uint8_t* st_seav(uint32_t router) const { return stamps + (uint64_t)router * st_stride; }
   uint8_t* st_ldca(uint32_t router) const { return stamps + (uint64_t)router * st_stride + st_seav_pad; }
@@ -473,24 +474,41 @@ static int fold_router(sp_ctx* ctx, uint32_t router) {
   return SP_OK;
 }
 
+// Selects a staging shape of the binned scan: its block count and the list
+// capacity the allocation gives it.
+static void set_binned_shape(sp_ctx* ctx, int index) {
+  ctx->bs.shape = sp::binned_shape(index);
+  ctx->bs_shape_index = (uint32_t)index;
+  ctx->bs.ctas = (uint32_t)sp::binned_ctas(ctx->bs.shape);
+  const uint64_t per_list = ctx->bs.list_words / ((uint64_t)(1u << ctx->p.k_log2) * ctx->bs.ctas);
+  ctx->bs.cap_alloc = (uint32_t)((per_list > 0xFFFFFFF8ull ? 0xFFFFFFF8ull : per_list) & ~7ull);
+}
+
 static int ensure_binned(sp_ctx* ctx, uint32_t router) {
   if (!ctx->bs.lists) {
-    ctx->bs.ctas = (uint32_t)sp::binned_ctas();
     ctx->bs.max_pairs = kBinnedRoundPairs;
     ctx->bs.fold_grid = sp::binned_fold_grid();
     const uint32_t bins = 1u << ctx->p.k_log2;
-    // room for the largest round: max_pairs split into host staging chunks
+    // room for the largest round of every shape: max_pairs split into host staging chunks
     const uint32_t chunks = (uint32_t)((ctx->bs.max_pairs + kStagingPairs - 1) / kStagingPairs);
-    const uint64_t cap = sp::binned_list_cap(ctx->bs.max_pairs, bins, ctx->bs.ctas, chunks);
-    if ((uint64_t)bins * ctx->bs.ctas * cap >= (1ull << 32)) return SP_ERR_PARAM;   // 32-bit list slots
-    ctx->bs.cap_alloc = (uint32_t)cap;
-    if (cudaMalloc(&ctx->bs.lists, (uint64_t)bins * ctx->bs.ctas * cap * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&ctx->bs.counts, (uint64_t)bins * ctx->bs.ctas * sizeof(uint32_t)) != cudaSuccess) {
+    uint64_t words = 0, max_ctas = 0;
+    for (int i = 0; i < sp::binned_shape_count(); ++i) {
+      const sp::BinShape h = sp::binned_shape(i);
+      const uint64_t ctas = (uint64_t)sp::binned_ctas(h);
+      const uint64_t w = (uint64_t)bins * ctas * sp::binned_list_cap(ctx->bs.max_pairs, bins, h, (uint32_t)ctas, chunks);
+      if (w > words) words = w;
+      if (ctas > max_ctas) max_ctas = ctas;
+    }
+    if (words >= (1ull << 32)) return SP_ERR_PARAM;   // 32-bit list slots
+    ctx->bs.list_words = words;
+    if (cudaMalloc(&ctx->bs.lists, words * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&ctx->bs.counts, (uint64_t)bins * max_ctas * sizeof(uint32_t)) != cudaSuccess) {
       cudaGetLastError();
       cudaFree(ctx->bs.lists);
       ctx->bs.lists = nullptr;
       return SP_ERR_NOMEM;
     }
+    set_binned_shape(ctx, (int)ctx->bs_shape_index);
   }
   if (!ctx->planes[router]) {
     if (cudaMalloc(&ctx->planes[router], sp::binned_planes_bytes(ctx->d)) != cudaSuccess) {
@@ -614,7 +632,7 @@ int sp_update_host(sp_ctx* ctx, uint32_t router, const uint32_t* host_pairs, uin
     const uint64_t round_n = binned ? ((n_pairs - done) < round_cap ? (n_pairs - done) : round_cap)
                                     : (n_pairs - done);
     const uint32_t chunks = (uint32_t)((round_n + kStagingPairs - 1) / kStagingPairs);
-    const uint32_t cap = binned ? sp::binned_list_cap(round_n, bins, ctx->bs.ctas, chunks) : 0u;
+    const uint32_t cap = binned ? sp::binned_list_cap(round_n, bins, ctx->bs.shape, ctx->bs.ctas, chunks) : 0u;
     const sp::BinnedScratch s = binned ? binned_scratch(ctx, router) : sp::BinnedScratch();
     uint64_t rdone = 0, rot = 0;
     for (uint32_t c = 0; rdone < round_n; ++c, ++j) {
@@ -629,7 +647,7 @@ int sp_update_host(sp_ctx* ctx, uint32_t router, const uint32_t* host_pairs, uin
         if (sp::binned_bin_chunk(ctx->d, ctx->seav(router), ctx->ldca(router), sp::bin_src_one(ctx->staging[b], m), s,
                                  cap, c > 0, (uint32_t)(rot % ctx->bs.ctas), ctx->stream) != cudaSuccess)
           return SP_ERR_CUDA;
-        rot += (m + sp::binned_tile_pairs() - 1) / sp::binned_tile_pairs();
+        rot += (m + sp::binned_tile_pairs(ctx->bs.shape) - 1) / sp::binned_tile_pairs(ctx->bs.shape);
       } else if ((rc = do_update(ctx, router, ctx->staging[b], m)) != SP_OK) {
         return rc;
       }
@@ -736,12 +754,13 @@ int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
       uint64_t sum = 0;
       while (j < mine.size() && sum + n_pairs[mine[j]] <= ctx->bs.max_pairs) {
         const uint32_t l = (uint32_t)((j + 1 - i + sp::kBinMaxSrc - 1) / sp::kBinMaxSrc);
-        if (j > i && sp::binned_list_cap(sum + n_pairs[mine[j]], bins, ctx->bs.ctas, l) > ctx->bs.cap_alloc) break;
+        if (j > i && sp::binned_list_cap(sum + n_pairs[mine[j]], bins, ctx->bs.shape, ctx->bs.ctas, l) >
+                         ctx->bs.cap_alloc) break;
         sum += n_pairs[mine[j++]];
       }
       // the round's batches, up to kBinMaxSrc streams per binning launch
       const uint32_t launches = (uint32_t)((j - i + sp::kBinMaxSrc - 1) / sp::kBinMaxSrc);
-      const uint32_t cap = sp::binned_list_cap(sum, bins, ctx->bs.ctas, launches);
+      const uint32_t cap = sp::binned_list_cap(sum, bins, ctx->bs.shape, ctx->bs.ctas, launches);
       const sp::BinnedScratch s = binned_scratch(ctx, r);
       uint64_t rot = 0;
       for (size_t q0 = i; q0 < j; q0 += sp::kBinMaxSrc) {
@@ -750,7 +769,7 @@ int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
         for (size_t q = q0; q < j && q < q0 + sp::kBinMaxSrc; ++q) {
           src.ptr[src.count] = dev_pairs[mine[q]];
           src.n[src.count] = n_pairs[mine[q]];
-          tiles += (n_pairs[mine[q]] + sp::binned_tile_pairs() - 1) / sp::binned_tile_pairs();
+          tiles += (n_pairs[mine[q]] + sp::binned_tile_pairs(ctx->bs.shape) - 1) / sp::binned_tile_pairs(ctx->bs.shape);
           ++src.count;
         }
         if (sp::binned_bin_chunk(ctx->d, ctx->seav(r), ctx->ldca(r), src, s, cap, q0 > i,
@@ -820,6 +839,73 @@ int sp_autotune(sp_ctx* ctx, const uint32_t* dev_pairs, uint64_t n_pairs, uint32
   if (rc != SP_OK) return rc;
   if (best_threads) *best_threads = (uint32_t)bt;
   if (best_blocks) *best_blocks = (uint32_t)(bg / (sms ? sms : 1));
+  rc = sp_reset(ctx, 0);
+  if (rc == SP_OK) rc = wait_stream(ctx);
+  return rc;
+}
+
+static sp_binned_shape shape_record(uint32_t index) {
+  const sp::BinShape h = sp::binned_shape((int)index);
+  return sp_binned_shape{index, h.threads, h.stage, h.tpr, h.per_sm, h.apply_threads};
+}
+
+int sp_binned_shapes(sp_binned_shape* out, uint32_t cap, uint32_t* n) {
+  if (!n || (cap && !out)) return SP_ERR_PARAM;
+  *n = (uint32_t)sp::binned_shape_count();
+  for (uint32_t i = 0; i < cap && i < *n; ++i) out[i] = shape_record(i);
+  return SP_OK;
+}
+
+int sp_set_binned_shape(sp_ctx* ctx, uint32_t index) {
+  if (!ctx || index >= (uint32_t)sp::binned_shape_count()) return SP_ERR_PARAM;
+  ctx->bs_shape_index = index;
+  if (ctx->bs.lists) set_binned_shape(ctx, (int)index);
+  return SP_OK;
+}
+
+int sp_get_binned_shape(const sp_ctx* ctx, sp_binned_shape* out) {
+  if (!ctx || !out) return SP_ERR_PARAM;
+  *out = shape_record(ctx->bs_shape_index);
+  return SP_OK;
+}
+
+int sp_autotune_binned(sp_ctx* ctx, const uint32_t* dev_pairs, uint64_t n_pairs, sp_binned_shape* best) {
+  if (!ctx || !dev_pairs || n_pairs == 0 || ((uintptr_t)dev_pairs & 7u)) return SP_ERR_PARAM;
+  if (!sp::binned_applicable(ctx->d)) return SP_ERR_STATE;
+  int rc = ensure_binned(ctx, 0);
+  if (rc != SP_OK) return rc;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return SP_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return SP_ERR_CUDA;
+  }
+  const uint32_t before = ctx->bs_shape_index;
+  uint32_t pick = before;
+  float best_ms = 1e30f;
+  auto scan = [&]() {
+    const sp::BinnedScratch s = binned_scratch(ctx, 0);
+    if (sp::launch_scan_binned(ctx->d, ctx->seav(0), ctx->ldca(0), dev_pairs, n_pairs, s, ctx->stream) != cudaSuccess)
+      return SP_ERR_CUDA;
+    ctx->planes_dirty[0] = true;
+    return SP_OK;
+  };
+  for (int i = 0; i < sp::binned_shape_count() && rc == SP_OK; ++i) {
+    set_binned_shape(ctx, i);
+    if ((rc = scan()) != SP_OK) break;                                  // warm up
+    if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { rc = SP_ERR_CUDA; break; }
+    for (int it = 0; it < 3 && rc == SP_OK; ++it) rc = scan();
+    if (rc != SP_OK || cudaEventRecord(e1, ctx->stream) != cudaSuccess) { rc = rc != SP_OK ? rc : SP_ERR_CUDA; break; }
+    float ms = 0.f;
+    if ((rc = wait_event_bounded(ctx, e1)) != SP_OK) break;
+    if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { rc = SP_ERR_CUDA; break; }
+    if (ms < best_ms) { best_ms = ms; pick = (uint32_t)i; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  set_binned_shape(ctx, (int)(rc == SP_OK ? pick : before));
+  if (rc != SP_OK) return rc;
+  if (best) *best = shape_record(pick);
   rc = sp_reset(ctx, 0);
   if (rc == SP_OK) rc = wait_stream(ctx);
   return rc;

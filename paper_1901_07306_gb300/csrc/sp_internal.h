@@ -65,14 +65,28 @@ struct BinSrc {
   uint32_t count;
 };
 
+// Staging shape of the binned scan (sp_scan_binned.cu); every compiled shape
+// gives the same bits, the autotuner picks the fastest.
+struct BinShape {
+  uint32_t threads;             // k_bin block size
+  uint32_t stage;               // staged hips per bin row
+  uint32_t tpr;                 // tiles per flush round
+  uint32_t per_sm;              // k_bin blocks per SM
+  uint32_t apply_threads;       // k_apply block size
+};
+int binned_shape_count();
+BinShape binned_shape(int i);   // i in [0, binned_shape_count()); 0 is the default
+
 // Scratch of the binned scan (sp_scan_binned.cu), shared by a context's routers.
 struct BinnedScratch {
   uint32_t* lists = nullptr;    // [bins][ctas][cap] hips
   uint32_t* counts = nullptr;   // [bins][ctas]
   uint32_t* planes = nullptr;   // plane accumulator of one router, [ceil(W / 8)][k][8] words, W = LR * LC / 32
   bool accumulate = false;      // planes hold earlier bits (load instead of zero)
-  uint32_t ctas = 0;            // persistent binning blocks
-  uint32_t cap_alloc = 0;       // hips per list the allocation holds: every launch's cap is clamped to it
+  BinShape shape{};             // staging shape of the launches
+  uint32_t ctas = 0;            // persistent binning blocks of this shape (SMs x per_sm)
+  uint32_t cap_alloc = 0;       // hips per list the allocation holds at this shape: every cap is clamped to it
+  uint64_t list_words = 0;      // hips the lists allocation holds
   uint64_t max_pairs = 0;       // pairs per binning round the lists are sized for
   int fold_grid = 0;
 };
@@ -88,8 +102,9 @@ cudaError_t launch_scan_multi(const DevParams& d, uint8_t* sketches, uint64_t st
                               int threads, int grid, cudaStream_t s);
 int multi_max_grid(int threads);
 bool binned_applicable(const DevParams& d);
-uint32_t binned_list_cap(uint64_t n_pairs, uint32_t bins, uint32_t ctas, uint32_t chunks);
-uint32_t binned_tile_pairs();
+// list capacity for a round of n_pairs binned by `chunks` launches of a shape
+uint32_t binned_list_cap(uint64_t n_pairs, uint32_t bins, const BinShape& shape, uint32_t ctas, uint32_t chunks);
+uint32_t binned_tile_pairs(const BinShape& shape);
 // bytes of one router's plane accumulator ([ceil(W / 8)][k][8] words)
 uint64_t binned_planes_bytes(const DevParams& d);
 // one binning launch over pairs[0, n) into the lists (append: continue them)
@@ -99,7 +114,7 @@ BinSrc bin_src_one(const uint32_t* pairs, uint64_t n_pairs);
 // the planes of the lists' hips (accumulate: on top of the pending planes)
 cudaError_t binned_apply_round(const DevParams& d, const BinnedScratch& s, uint32_t cap, bool accumulate,
                                cudaStream_t st);
-int binned_ctas();
+int binned_ctas(const BinShape& shape);
 int binned_fold_grid();
 // scan with the LDCA bits accumulated in s.planes (no fold)
 cudaError_t launch_scan_binned(const DevParams& d, uint8_t* seav, uint32_t* ldca, const uint32_t* pairs,

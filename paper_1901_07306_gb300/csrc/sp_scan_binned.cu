@@ -5,7 +5,7 @@
 // "plane b" the set of bit b of every LDC: LR x LC bits (32 KiB at k = 1024,
 // LR = 4, LC = 2^16).  A pair touches exactly one plane, so:
 //
-//  k_bin    (persistent, one 1024-thread block per SM) streams 8K-pair tiles
+//  k_bin    (persistent, one or two blocks per SM, shapes below) streams tiles
 //           with 16-byte loads held in registers (the next tile's loads are
 //           issued before the current tile's work), does the SEAV update of
 //           Sec. 3.1-3.2 for sampled pairs (L2 RED, 1 pair in 2^tau), and
@@ -27,6 +27,13 @@
 //
 // Applicable when the bins are the LDC's k bit positions (k <= 1024) and one
 // plane fits in shared memory as whole words (LC >= 32, LR x LC <= 2^20 bits).
+//
+// Staging shapes (the autotuner picks one per context; every shape gives the
+// same bits):  k_bin block size, staging row length, tiles per flush round
+// and blocks per SM -- a 1024-thread block with 44-hip rows flushing every two
+// tiles, or two 512-thread blocks per SM with 20-hip rows flushing every tile,
+// so one block's flush overlaps the other's hashing -- and the k_apply block
+// size.
 #include <math.h>
 
 #include "sp_internal.h"
@@ -35,15 +42,9 @@ namespace sp {
 
 namespace {
 
-constexpr int kBinThreads = 1024;
 constexpr int kVec = 4;                            // 16-byte loads (2 pairs) per thread and tile
-constexpr int kTile = kBinThreads * kVec * 2;      // 8192 pairs per block iteration
 constexpr int kGroup = 4;                          // pairs hashed and staged together
 constexpr int kChunk = 8;                          // hips per list store (32 bytes)
-constexpr int kStage = 44;                         // staged hips per bin (176-byte rows:
-                                                   // 16-byte lane accesses hit all 32 banks)
-constexpr int kQueue = 512;                        // sampled pairs queued per round of 2 tiles
-constexpr int kApplyThreads = 512;
 constexpr int kApplyUnroll = 8;                    // hip loads in flight per lane
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
@@ -58,14 +59,17 @@ __device__ __forceinline__ void seav_set(const DevParams& d, uint8_t* seav, uint
   }
 }
 
-template <int LR>
+// One L2 RED per LDCA row: the rare overflow path of k_bin (a full staging
+// row or list), so the row count is read at run time.
 __device__ __forceinline__ void ldca_red(const DevParams& d, uint32_t* ldca, uint32_t hip, uint32_t h3) {
   const uint32_t cshift = 32u - d.lc_log2;
   const uint32_t wshift = d.k_log2 - 5u;
 #pragma unroll
-  for (int i = 0; i < LR; ++i) {
-    const uint32_t col = (uint32_t)((uint64_t)mas(d.ha[2 + i], d.hb[2 + i], hip) >> cshift);
-    atomicOr(ldca + (((uint64_t)(((uint32_t)i << d.lc_log2) | col) << wshift) | (h3 >> 5)), 1u << (h3 & 31u));
+  for (uint32_t i = 0; i < 8; ++i) {               // constant indices into the parameter block
+    if (i < d.lr) {
+      const uint32_t col = (uint32_t)((uint64_t)mas(d.ha[2 + i], d.hb[2 + i], hip) >> cshift);
+      atomicOr(ldca + (((uint64_t)((i << d.lc_log2) | col) << wshift) | (h3 >> 5)), 1u << (h3 & 31u));
+    }
   }
 }
 
@@ -76,34 +80,37 @@ __device__ __forceinline__ void st_chunk(uint32_t* dst, uint4 a, uint4 b) {
                : "memory");
 }
 
-// k_bin: tiles of kTile pairs, tile (slot + i G) in iteration i.  Each
+// k_bin: tiles of TILE = THREADS * 2 kVec pairs, tile (slot + i G) in iteration i.  Each
 // thread holds kVec 16-byte loads (2 pairs each) of a tile in registers and
 // issues the loads of tile i + 1 before it works on tile i, so the copy from
 // HBM overlaps the work.  Tiles that are partial, or a stream that is not
 // 16-byte aligned, are read pair by pair instead.  Every bin owns a staging
-// row of kStage hips in shared memory that persists across tiles (a
+// row of STAGE hips in shared memory that persists across tiles (a
 // write-combining buffer for the bin's list).  Per tile:
 //   1. every thread hashes its pairs, queues the sampled pairs (Sec. 3.1) for
 //      a converged SEAV pass, takes a place in its pair's bin row with one
 //      shared atomic and stores the hip there (a row that is full sends the
 //      pair to L2 REDs instead);
-//   2. each thread takes bins tid, tid + kBinThreads, ...: it moves the row's
+//   2. (after every TPR tiles) each thread takes bins tid, tid + THREADS, ...:
+//      it moves the row's
 //      whole 8-hip chunks to the bin's list with 32-byte stores and keeps the
 //      remainder (< 8 hips) at the front of the row; the queued pairs set
 //      their SEAV bits.
 // At the end the remainders go to the lists with plain stores; an appending
 // launch first takes the tail of a list that is not a whole chunk back into
 // the row, so lists stay dense and chunk stores stay 32-byte aligned.
-template <int LR>
-__global__ void __launch_bounds__(kBinThreads, 1)
+template <int THREADS, int STAGE, int TPR, int PER_SM>
+__global__ void __launch_bounds__(THREADS, PER_SM)
 k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
       BinSrc src, uint32_t* __restrict__ lists, uint32_t* __restrict__ counts, uint32_t cap,
       bool append, uint32_t rot) {
+  constexpr int TILE = THREADS * kVec * 2;
+  constexpr int QUEUE = TPR * TILE / 32;              // sampled pairs per round: 4x the expected 2^-7
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const uint32_t bins = 1u << d.k_log2;                                // <= 1024
-  uint32_t* stage = reinterpret_cast<uint32_t*>(smem_raw);             // [bins][kStage]
-  uint2* s_queue = reinterpret_cast<uint2*>(stage + bins * kStage);   // [kQueue] sampled (hip, h1)
-  uint32_t* s_fill = reinterpret_cast<uint32_t*>(s_queue + kQueue);    // [bins] hips in the row
+  uint32_t* stage = reinterpret_cast<uint32_t*>(smem_raw);             // [bins][STAGE]
+  uint2* s_queue = reinterpret_cast<uint2*>(stage + bins * STAGE);    // [QUEUE] sampled (hip, h1)
+  uint32_t* s_fill = reinterpret_cast<uint32_t*>(s_queue + QUEUE);     // [bins] hips in the row
   uint32_t* s_cursor = s_fill + bins;                                   // [bins] list fill (whole chunks)
   __shared__ uint32_t s_qn[2];                                          // queue fill, by tile parity
   __shared__ uint64_t s_tpref[kBinMaxSrc + 1];
@@ -117,17 +124,17 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
     uint64_t acc = 0;
     s_tpref[0] = 0;
     for (uint32_t b = 0; b < src.count; ++b) {
-      acc += (src.n[b] + kTile - 1) / kTile;
+      acc += (src.n[b] + TILE - 1) / TILE;
       s_tpref[b + 1] = acc;
     }
     s_qn[0] = s_qn[1] = 0;
   }
   auto list_of = [&](uint32_t b) { return lists + ((uint64_t)b * G + cta) * cap; };
-  for (uint32_t b = tid; b < bins; b += kBinThreads) {
+  for (uint32_t b = tid; b < bins; b += THREADS) {
     // an appending launch continues the list: its partial chunk returns to the row
     const uint32_t have = append ? counts[(uint64_t)b * G + cta] : 0u;
     const uint32_t tail = have & (kChunk - 1u);
-    for (uint32_t e = 0; e < tail; ++e) stage[b * kStage + e] = list_of(b)[have - tail + e];
+    for (uint32_t e = 0; e < tail; ++e) stage[b * STAGE + e] = list_of(b)[have - tail + e];
     s_fill[b] = tail;
     s_cursor[b] = have - tail;
   }
@@ -141,12 +148,12 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
     uint32_t b = stream_hint;
     while (s_tpref[b + 1] <= tile) ++b;
     stream_hint = b;
-    const uint64_t base = (tile - s_tpref[b]) * kTile;
+    const uint64_t base = (tile - s_tpref[b]) * TILE;
     const uint64_t left = src.n[b] - base;
     TileRef t;
     t.p = reinterpret_cast<const uint2*>(src.ptr[b]) + base;
-    t.n = left < (uint64_t)kTile ? (uint32_t)left : (uint32_t)kTile;
-    t.vec = ((uintptr_t)src.ptr[b] & 15u) == 0 && t.n == (uint32_t)kTile;
+    t.n = left < (uint64_t)TILE ? (uint32_t)left : (uint32_t)TILE;
+    t.vec = ((uintptr_t)src.ptr[b] & 15u) == 0 && t.n == (uint32_t)TILE;
     return t;
   };
   // 16-byte streaming loads of this thread's share of a whole tile; volatile,
@@ -156,7 +163,7 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
 #pragma unroll
     for (int u = 0; u < kVec; ++u)
       asm volatile("ld.global.cs.v4.u32 {%0, %1, %2, %3}, [%4];"
-                   : "=r"(r[u].x), "=r"(r[u].y), "=r"(r[u].z), "=r"(r[u].w) : "l"(p4 + u * kBinThreads));
+                   : "=r"(r[u].x), "=r"(r[u].y), "=r"(r[u].z), "=r"(r[u].w) : "l"(p4 + u * THREADS));
   };
   // step 1 for a group of kGroup pairs (valid: bit q = pair q exists):
   // hashes, the sampled-pair queue (one warp-aggregated push per pair
@@ -174,7 +181,7 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
         uint32_t first = 0;
         if (lane == 0) first = atomicAdd(&s_qn[par], (uint32_t)__popc(ballot));
         first = __shfl_sync(kFull, first, 0) + (uint32_t)__popc(ballot & ((1u << lane) - 1u));
-        if (((ballot >> lane) & 1u) && first < (uint32_t)kQueue) s_queue[first] = make_uint2(hip[q], h1);
+        if (((ballot >> lane) & 1u) && first < (uint32_t)QUEUE) s_queue[first] = make_uint2(hip[q], h1);
         else if ((ballot >> lane) & 1u) over |= 1u << (kGroup + q);   // queue full: SEAV bits directly
       }
       bin[q] = mas(d.ha[1], d.hb[1], oip[q]) >> h3_shift;
@@ -184,8 +191,8 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
       at[q] = ((valid >> q) & 1u) ? atomicAdd(&s_fill[bin[q]], 1u) : 0xFFFFu;
 #pragma unroll
     for (int q = 0; q < kGroup; ++q) {
-      if (at[q] < (uint32_t)kStage) stage[bin[q] * kStage + at[q]] = hip[q];
-      over |= (at[q] >= (uint32_t)kStage && at[q] != 0xFFFFu ? 1u : 0u) << q;
+      if (at[q] < (uint32_t)STAGE) stage[bin[q] * STAGE + at[q]] = hip[q];
+      over |= (at[q] >= (uint32_t)STAGE && at[q] != 0xFFFFu ? 1u : 0u) << q;
     }
     return over;
   };
@@ -196,14 +203,14 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
     if (__any_sync(kFull, over != 0u)) {
 #pragma unroll
       for (int q = 0; q < kGroup; ++q) {
-        if ((over >> q) & 1u) ldca_red<LR>(d, ldca, hip[q], bin[q]);
+        if ((over >> q) & 1u) ldca_red(d, ldca, hip[q], bin[q]);
         if ((over >> (kGroup + q)) & 1u) seav_set(d, seav, hip[q], mas(d.ha[0], d.hb[0], oip[q]));
       }
     }
   };
-  // whole chunks of bin b's row (fill f <= kStage) to its list, remainder to the front
+  // whole chunks of bin b's row (fill f <= STAGE) to its list, remainder to the front
   auto flush_row = [&](uint32_t b, uint32_t f) {
-    uint32_t* row = stage + b * kStage;
+    uint32_t* row = stage + b * STAGE;
     uint32_t* list = list_of(b);
     uint32_t cur = s_cursor[b];
     const uint32_t nch = f / kChunk;
@@ -215,11 +222,11 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
         cur += kChunk;
       } else {                                      // list full: straight to L2
         const uint32_t h[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
-        for (int e = 0; e < 8; ++e) ldca_red<LR>(d, ldca, h[e], b);
+        for (int e = 0; e < 8; ++e) ldca_red(d, ldca, h[e], b);
       }
     }
     const uint32_t rem = f - nch * kChunk;
-    for (uint32_t e = 0; e < rem; e += 4)           // within the row: nch * 8 + rem <= kStage
+    for (uint32_t e = 0; e < rem; e += 4)           // within the row: nch * 8 + rem <= STAGE
       *reinterpret_cast<uint4*>(row + e) = *reinterpret_cast<const uint4*>(row + nch * kChunk + e);
     s_fill[b] = rem;
     s_cursor[b] = cur;
@@ -240,11 +247,11 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
         group_leftovers(hip, oip, bin, over);
       }
     } else {
-      for (uint32_t j0 = 0; j0 < (uint32_t)kTile; j0 += kGroup * kBinThreads) {
+      for (uint32_t j0 = 0; j0 < (uint32_t)TILE; j0 += kGroup * THREADS) {
         uint32_t hip[kGroup], oip[kGroup], bin[kGroup], valid = 0;
 #pragma unroll
         for (int q = 0; q < kGroup; ++q) {
-          const uint32_t j = j0 + (uint32_t)q * kBinThreads + tid;
+          const uint32_t j = j0 + (uint32_t)q * THREADS + tid;
           uint2 v = make_uint2(0u, 0u);
           if (j < t.n) { v = __ldcs(t.p + j); valid |= 1u << q; }
           hip[q] = v.x; oip[q] = v.y;
@@ -254,9 +261,25 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
       }
     }
   };
-  // Rounds of two tiles (i, i + 1) with one flush: the two register buffers
-  // alternate, and each tile's loads go out before the work on the tile
-  // before it.
+  // the flush round: whole chunks to the lists; the queued SEAV updates,
+  // spread over the warps
+  auto flush_round = [&](uint32_t par) {
+    __syncthreads();
+    const uint32_t qn = s_qn[par] < (uint32_t)QUEUE ? s_qn[par] : (uint32_t)QUEUE;
+    if (tid == 0) s_qn[par ^ 1u] = 0;            // read by every thread before the last barrier
+    for (uint32_t b = tid; b < bins; b += THREADS) {
+      const uint32_t f = s_fill[b];
+      if (f >= (uint32_t)kChunk) flush_row(b, f < (uint32_t)STAGE ? f : (uint32_t)STAGE);
+    }
+    for (uint32_t e = (tid & 31u) * (THREADS / 32u) + (tid >> 5); e < qn; e += THREADS) {   // a bijection on [0, THREADS)
+      const uint2 x = s_queue[e];
+      seav_set(d, seav, x.x, x.y);
+    }
+    __syncthreads();
+  };
+  // Tiles in pairs (i, i + 1): the two register buffers alternate, and each
+  // tile's loads go out before the work on the tile before it; a flush round
+  // after every TPR tiles.
   uint4 ra[kVec], rb[kVec];
   TileRef ta{nullptr, 0u, false}, tb{nullptr, 0u, false};
   if (tile_of(0) < n_tiles) {
@@ -264,55 +287,48 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
     if (ta.vec) load_tile(ra, ta.p);
   }
   uint32_t par = 0;
-  for (uint64_t i = 0; tile_of(i) < n_tiles; i += 2, par ^= 1u) {
+  for (uint64_t i = 0; tile_of(i) < n_tiles; i += 2) {
     const bool has_b = tile_of(i + 1) < n_tiles;
     if (has_b) {
       tb = tile_ref(tile_of(i + 1));
       if (tb.vec) load_tile(rb, tb.p);
     }
     stage_tile(ra, ta, par);
+    if (TPR == 1) {
+      flush_round(par);
+      par ^= 1u;
+    }
     if (tile_of(i + 2) < n_tiles) {
       ta = tile_ref(tile_of(i + 2));
       if (ta.vec) load_tile(ra, ta.p);
     }
     if (has_b) stage_tile(rb, tb, par);
-    __syncthreads();
-    // 2. whole chunks to the lists; the queued SEAV updates, spread over the warps
-    const uint32_t qn = s_qn[par] < (uint32_t)kQueue ? s_qn[par] : (uint32_t)kQueue;
-    if (tid == 0) s_qn[par ^ 1u] = 0;            // read by every thread before the last barrier
-    for (uint32_t b = tid; b < bins; b += kBinThreads) {
-      const uint32_t f = s_fill[b];
-      if (f >= (uint32_t)kChunk) flush_row(b, f < (uint32_t)kStage ? f : (uint32_t)kStage);
-    }
-    for (uint32_t e = (tid & 31u) * 32u + (tid >> 5); e < qn; e += kBinThreads) {
-      const uint2 x = s_queue[e];
-      seav_set(d, seav, x.x, x.y);
-    }
-    __syncthreads();
+    flush_round(par);
+    par ^= 1u;
   }
   // remainders (< 8 hips per row) with plain stores
-  for (uint32_t b = tid; b < bins; b += kBinThreads) {
+  for (uint32_t b = tid; b < bins; b += THREADS) {
     const uint32_t f = s_fill[b];
     uint32_t* list = list_of(b);
     uint32_t c = s_cursor[b];
     for (uint32_t e = 0; e < f; ++e) {
-      const uint32_t h = stage[b * kStage + e];
+      const uint32_t h = stage[b * STAGE + e];
       if (c < cap) list[c++] = h;
-      else ldca_red<LR>(d, ldca, h, b);
+      else ldca_red(d, ldca, h, b);
     }
     counts[(uint64_t)b * G + cta] = c;
   }
 }
 
-template <int LR>
-__global__ void __launch_bounds__(kApplyThreads)
+template <int LR, int THREADS>
+__global__ void __launch_bounds__(THREADS)
 k_apply(DevParams d, const uint32_t* __restrict__ lists, const uint32_t* __restrict__ counts,
         uint32_t G, uint32_t cap, uint32_t* __restrict__ planes, bool accumulate) {
   extern __shared__ uint32_t s_plane[];
   const uint32_t b = blockIdx.x;
   const uint32_t words = ((uint32_t)LR << d.lc_log2) >> 5;       // plane words
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  const uint32_t nwarps = kApplyThreads / 32;
+  const uint32_t nwarps = THREADS / 32;
   // LH_i(hip) = h >> cshift (5 <= lc_log2 <= 20): LDC h >> cshift of row i is
   // bit (h >> cshift) mod 32 of plane word (i << (lc_log2 - 5)) + (h >> (cshift + 5))
   const uint32_t cshift = 32u - d.lc_log2;
@@ -322,7 +338,7 @@ k_apply(DevParams d, const uint32_t* __restrict__ lists, const uint32_t* __restr
   const uint64_t chunk_stride = (uint64_t)(1u << d.k_log2) * 8u;
   uint32_t* dst = planes + (uint64_t)b * 8u;
   auto at_word = [&](uint32_t w) { return dst + (uint64_t)(w >> 3) * chunk_stride + (w & 7u); };
-  for (uint32_t w = tid; w < words; w += kApplyThreads) s_plane[w] = accumulate ? *at_word(w) : 0u;
+  for (uint32_t w = tid; w < words; w += THREADS) s_plane[w] = accumulate ? *at_word(w) : 0u;
   __syncthreads();
   auto set_bits = [&](uint32_t hip) {
 #pragma unroll
@@ -356,7 +372,7 @@ k_apply(DevParams d, const uint32_t* __restrict__ lists, const uint32_t* __restr
     }
   }
   __syncthreads();
-  for (uint32_t w = tid; w < words; w += kApplyThreads) *at_word(w) = s_plane[w];
+  for (uint32_t w = tid; w < words; w += THREADS) *at_word(w) = s_plane[w];
 }
 
 // 32 x 32 bit transpose across a warp: lane l holds row l (bit j = column j);
@@ -463,27 +479,35 @@ k_fold8(const uint32_t* __restrict__ planes, uint32_t* __restrict__ ldca, uint32
   }
 }
 
-template <int LR>
+template <int THREADS, int STAGE, int TPR, int PER_SM>
 cudaError_t bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const BinSrc& src,
                       const BinnedScratch& s, uint32_t cap, bool append, uint32_t rot, cudaStream_t st) {
   const uint32_t bins = 1u << d.k_log2;
   // the bins' staging rows, the sampled-pair queue, 2 counters per bin
-  const size_t bin_smem = (size_t)bins * kStage * 4 + (size_t)kQueue * 8 + (size_t)bins * 8;
-  cudaError_t e = cudaFuncSetAttribute(k_bin<LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
+  const size_t bin_smem = (size_t)bins * STAGE * 4 + (size_t)(TPR * THREADS * kVec * 2 / 32) * 8 + (size_t)bins * 8;
+  auto kern = k_bin<THREADS, STAGE, TPR, PER_SM>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
   if (e != cudaSuccess) return e;
-  k_bin<LR><<<s.ctas, kBinThreads, bin_smem, st>>>(d, seav, ldca, src, s.lists, s.counts, cap, append, rot);
+  kern<<<s.ctas, THREADS, bin_smem, st>>>(d, seav, ldca, src, s.lists, s.counts, cap, append, rot);
+  return cudaGetLastError();
+}
+
+template <int LR, int THREADS>
+cudaError_t apply_round_t(const DevParams& d, const BinnedScratch& s, uint32_t cap, bool accumulate, cudaStream_t st) {
+  const uint32_t bins = 1u << d.k_log2;
+  const uint32_t words = ((uint32_t)LR << d.lc_log2) >> 5;
+  const size_t apply_smem = (size_t)words * sizeof(uint32_t);
+  cudaError_t e = cudaFuncSetAttribute(k_apply<LR, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)apply_smem);
+  if (e != cudaSuccess) return e;
+  k_apply<LR, THREADS><<<bins, THREADS, apply_smem, st>>>(d, s.lists, s.counts, s.ctas, cap, s.planes, accumulate);
   return cudaGetLastError();
 }
 
 template <int LR>
 cudaError_t apply_round(const DevParams& d, const BinnedScratch& s, uint32_t cap, bool accumulate, cudaStream_t st) {
-  const uint32_t bins = 1u << d.k_log2;
-  const uint32_t words = ((uint32_t)LR << d.lc_log2) >> 5;
-  const size_t apply_smem = (size_t)words * sizeof(uint32_t);
-  cudaError_t e = cudaFuncSetAttribute(k_apply<LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_smem);
-  if (e != cudaSuccess) return e;
-  k_apply<LR><<<bins, kApplyThreads, apply_smem, st>>>(d, s.lists, s.counts, s.ctas, cap, s.planes, accumulate);
-  return cudaGetLastError();
+  return s.shape.apply_threads == 256 ? apply_round_t<LR, 256>(d, s, cap, accumulate, st)
+                                      : apply_round_t<LR, 512>(d, s, cap, accumulate, st);
 }
 
 }  // namespace
@@ -493,29 +517,45 @@ bool binned_applicable(const DevParams& d) {
   return d.k_log2 >= 5 && d.k_log2 <= 10 && d.lc_log2 >= 5 && plane_bits <= (1ull << 20);
 }
 
+// The compiled staging shapes: {k_bin threads, row hips, tiles per flush
+// round, blocks per SM, k_apply threads}.  Rows hold 4 x odd hips, so the
+// flush's 16-byte row reads of 8 consecutive bins hit all 32 banks; a row
+// holds the < 8 hips a flush leaves plus a round's arrivals with headroom
+// (one block per SM: 2 tiles of 8K pairs, 16 per bin on average, 44-hip rows;
+// two per SM: 1 tile of 4K pairs, 20-hip rows).
+constexpr BinShape kShapes[] = {
+  {1024, 44, 2, 1, 512}, {1024, 44, 2, 1, 256},
+  {512, 20, 1, 2, 512},  {512, 20, 1, 2, 256},
+  {512, 20, 2, 2, 512},  {512, 20, 2, 2, 256},
+};
+
+int binned_shape_count() { return (int)(sizeof(kShapes) / sizeof(kShapes[0])); }
+BinShape binned_shape(int i) { return kShapes[(i >= 0 && i < binned_shape_count()) ? i : 0]; }
+
 // List capacity for a round of n_pairs split into `chunks` binning launches:
 // a block takes at most ceil(tiles / ctas) + 1 tiles per launch (the tile to
 // block mapping rotates between launches), spread over the bins; 8 standard
 // deviations plus 32 of headroom, so that only skewed inputs overflow.
-uint32_t binned_list_cap(uint64_t n_pairs, uint32_t bins, uint32_t ctas, uint32_t chunks) {
-  const uint64_t tiles = (n_pairs + kTile - 1) / kTile;
+uint32_t binned_list_cap(uint64_t n_pairs, uint32_t bins, const BinShape& shape, uint32_t ctas, uint32_t chunks) {
+  const uint64_t tile = binned_tile_pairs(shape);
+  const uint64_t tiles = (n_pairs + tile - 1) / tile;
   const uint64_t per_cta = (tiles + ctas - 1) / ctas + (chunks > 1 ? chunks : 1);
-  const double m = (double)(per_cta * kTile < n_pairs ? per_cta * kTile : n_pairs) / bins;
+  const double m = (double)(per_cta * tile < n_pairs ? per_cta * tile : n_pairs) / bins;
   uint64_t cap = (uint64_t)(m + 8.0 * sqrt(m + 1.0) + 32.0);
   cap = (cap + 7) & ~7ull;                                   // 32-byte list starts
   return (uint32_t)cap;
 }
 
-int binned_ctas() {
+static int sm_count() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   return sms;
 }
 
-int binned_fold_grid() {
-  return binned_ctas() * 8;
-}
+int binned_ctas(const BinShape& shape) { return sm_count() * (int)shape.per_sm; }
+
+int binned_fold_grid() { return sm_count() * 8; }
 
 cudaError_t launch_fold(const DevParams& d, const uint32_t* planes, uint32_t* ldca, int grid, cudaStream_t st) {
   const uint32_t words = (uint32_t)(((uint64_t)d.lr << d.lc_log2) >> 5);
@@ -538,16 +578,10 @@ cudaError_t binned_bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, 
   // the list stride never exceeds what was allocated (hips past a full list go
   // to L2 REDs, so a smaller cap only costs speed)
   if (cap > s.cap_alloc) cap = s.cap_alloc;
-  switch (d.lr) {
-    case 1: return bin_chunk<1>(d, seav, ldca, src, s, cap, append, rot, st);
-    case 2: return bin_chunk<2>(d, seav, ldca, src, s, cap, append, rot, st);
-    case 3: return bin_chunk<3>(d, seav, ldca, src, s, cap, append, rot, st);
-    case 4: return bin_chunk<4>(d, seav, ldca, src, s, cap, append, rot, st);
-    case 5: return bin_chunk<5>(d, seav, ldca, src, s, cap, append, rot, st);
-    case 6: return bin_chunk<6>(d, seav, ldca, src, s, cap, append, rot, st);
-    case 7: return bin_chunk<7>(d, seav, ldca, src, s, cap, append, rot, st);
-    default: return bin_chunk<8>(d, seav, ldca, src, s, cap, append, rot, st);
-  }
+  const BinShape& h = s.shape;
+  if (h.threads == 512 && h.tpr == 1) return bin_chunk<512, 20, 1, 2>(d, seav, ldca, src, s, cap, append, rot, st);
+  if (h.threads == 512) return bin_chunk<512, 20, 2, 2>(d, seav, ldca, src, s, cap, append, rot, st);
+  return bin_chunk<1024, 44, 2, 1>(d, seav, ldca, src, s, cap, append, rot, st);
 }
 
 cudaError_t binned_apply_round(const DevParams& d, const BinnedScratch& s, uint32_t cap, bool accumulate,
@@ -565,7 +599,7 @@ cudaError_t binned_apply_round(const DevParams& d, const BinnedScratch& s, uint3
   }
 }
 
-uint32_t binned_tile_pairs() { return (uint32_t)kTile; }
+uint32_t binned_tile_pairs(const BinShape& shape) { return shape.threads * (uint32_t)kVec * 2u; }
 
 uint64_t binned_planes_bytes(const DevParams& d) {
   const uint64_t words = ((uint64_t)d.lr << d.lc_log2) >> 5;          // per plane
@@ -578,7 +612,7 @@ cudaError_t launch_scan_binned(const DevParams& d, uint8_t* seav, uint32_t* ldca
   bool accumulate = s.accumulate;
   while (done < n_pairs) {
     const uint64_t n = (n_pairs - done) < s.max_pairs ? (n_pairs - done) : s.max_pairs;
-    const uint32_t cap = binned_list_cap(n, 1u << d.k_log2, s.ctas, 1);
+    const uint32_t cap = binned_list_cap(n, 1u << d.k_log2, s.shape, s.ctas, 1);
     cudaError_t e = binned_bin_chunk(d, seav, ldca, bin_src_one(pairs + 2 * done, n), s, cap, false, 0, st);
     if (e == cudaSuccess) e = binned_apply_round(d, s, cap, accumulate, st);
     if (e != cudaSuccess) return e;

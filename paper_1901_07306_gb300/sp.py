@@ -42,6 +42,7 @@ EXPORTED = (
     "sp_detect_async", "sp_results", "sp_detect", "sp_results_device", "sp_slide",
     "sp_export", "sp_import", "sp_detect_noalloc", "sp_update_batched_device", "sp_autotune",
     "sp_results_async", "sp_psu", "sp_size_ldca", "sp_set_timeout", "sp_copy_sketch", "sp_merge_device",
+    "sp_binned_shapes", "sp_set_binned_shape", "sp_get_binned_shape", "sp_autotune_binned",
 )
 
 
@@ -59,6 +60,15 @@ class sp_params(ctypes.Structure):
 class sp_candidate(ctypes.Structure):
     _fields_ = [("ip", ctypes.c_uint32), ("z0", ctypes.c_uint32), ("est", ctypes.c_double),
                 ("flags", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+
+
+class sp_binned_shape(ctypes.Structure):
+    _fields_ = [("index", ctypes.c_uint32), ("bin_threads", ctypes.c_uint32), ("bin_stage", ctypes.c_uint32),
+                ("bin_tiles_per_round", ctypes.c_uint32), ("bin_blocks_per_sm", ctypes.c_uint32),
+                ("apply_threads", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class sp_batch(ctypes.Structure):
@@ -102,6 +112,10 @@ def _load():
         "sp_merge": (i32, [vp, P(u32), u32, u32]),
         "sp_copy_sketch": (i32, [vp, u32, vp, u64, P(u64)]),
         "sp_merge_device": (i32, [vp, P(vp), u32, u32]),
+        "sp_binned_shapes": (i32, [P(sp_binned_shape), u32, P(u32)]),
+        "sp_set_binned_shape": (i32, [vp, u32]),
+        "sp_get_binned_shape": (i32, [vp, P(sp_binned_shape)]),
+        "sp_autotune_binned": (i32, [vp, vp, u64, P(sp_binned_shape)]),
         "sp_detect_async": (i32, [vp, u32, u32]),
         "sp_results": (i32, [vp, vp, u64, P(u64)]),
         "sp_detect": (i32, [vp, u32, u32, vp, u64, P(u64)]),
@@ -272,6 +286,34 @@ def sp_autotune(ctx: int, dev_pairs):
     _check(lib.sp_autotune(ctypes.c_void_p(ctx), ctypes.c_void_p(ptr), n, ctypes.byref(t), ctypes.byref(b)),
            "sp_autotune")
     return t.value, b.value
+
+
+def sp_binned_shapes() -> list:
+    n = ctypes.c_uint32()
+    _check(lib.sp_binned_shapes(None, 0, ctypes.byref(n)), "sp_binned_shapes")
+    out = (sp_binned_shape * n.value)()
+    _check(lib.sp_binned_shapes(out, n.value, ctypes.byref(n)), "sp_binned_shapes")
+    return [x.as_dict() for x in out]
+
+
+def sp_set_binned_shape(ctx: int, index: int) -> None:
+    _check(lib.sp_set_binned_shape(ctypes.c_void_p(ctx), index), "sp_set_binned_shape")
+
+
+def sp_get_binned_shape(ctx: int) -> dict:
+    out = sp_binned_shape()
+    _check(lib.sp_get_binned_shape(ctypes.c_void_p(ctx), ctypes.byref(out)), "sp_get_binned_shape")
+    return out.as_dict()
+
+
+def sp_autotune_binned(ctx: int, dev_pairs) -> dict:
+    """Times every compiled staging shape of the binned scan on the sample,
+    keeps the fastest; returns its description."""
+    ptr, n = _pairs_ptr(dev_pairs)
+    out = sp_binned_shape()
+    _check(lib.sp_autotune_binned(ctypes.c_void_p(ctx), ctypes.c_void_p(ptr), n, ctypes.byref(out)),
+           "sp_autotune_binned")
+    return out.as_dict()
 
 
 def sp_merge(ctx: int, routers, dst_router: int) -> None:

@@ -332,3 +332,58 @@ def test_core_link_full_size(sp, torch, mode):
         assert_same_results(got, want)
         recall = len(set(planted.tolist()) & set(got["ip"].tolist())) / len(planted)
         assert recall > 0.95
+
+
+def _shape_count(sp):
+    return len(sp.sp_binned_shapes())
+
+
+@pytest.mark.parametrize("shape", range(6))
+def test_every_binned_shape_is_bit_exact(sp, torch, shape):
+    """Every compiled staging shape of the binned scan gives the oracle's
+    sketch: unaligned head, a ragged last tile, appending launches (host
+    path chunks and a batched call of many streams), pending planes, a
+    skewed stream that overflows rows and lists, and a detect."""
+    if shape >= _shape_count(sp):
+        pytest.skip("fewer compiled shapes")
+    kw = dict(theta=256, seed=41, n_routers=2, scan_mode=2)
+    op = oracle_params(kw)
+    a, planted = W.single_window(seed=41, n=(1 << 20) + 12345, n_background=16384, n_planted=6, planted_degree=900)
+    n = 1 << 18
+    rng = np.random.default_rng(41)
+    skew = np.stack([rng.integers(0, 2**32, n, dtype=np.uint32), np.full(n, 0x0A000001, np.uint32)], 1)
+    parts = np.array_split(W.uniform_pairs(600000, seed=42, n_hosts=30000), 40)
+    with sp.SuperPoint(**kw) as ctx:
+        sp.sp_set_binned_shape(ctx.ctx, shape)
+        assert sp.sp_get_binned_shape(ctx.ctx)["index"] == shape
+        ctx.update(dev(torch, a, 1), router=0)                              # 8 bytes off a 16-byte boundary
+        ctx.update(dev(torch, skew), router=0)                              # on pending planes, rows overflow
+        host = torch.from_numpy(a.reshape(-1).view(np.int32).copy()).pin_memory()
+        ctx.update_host(host, router=1)
+        sp.sp_update_batched(ctx.ctx, [1] * len(parts), [dev(torch, x) for x in parts])
+        osk0 = O.Sketch(op).update(a).update(skew)
+        assert_same_sketch(ctx, osk0, router=0)
+        osk1 = O.Sketch(op).update(a).update(np.concatenate(parts))
+        assert_same_sketch(ctx, osk1, router=1)
+        got, n_got, rc = ctx.detect(router=1)
+        want, _, _ = osk1.detect()
+        assert_same_results(got, want)
+
+
+def test_autotune_binned_picks_a_shape_and_stays_exact(sp, torch):
+    pairs, planted = W.core_link(seed=43, n=1 << 22)
+    kw = dict(seed=43, scan_mode=2)
+    with sp.SuperPoint(**kw) as ctx:
+        best = sp.sp_autotune_binned(ctx.ctx, dev(torch, pairs))
+        assert 0 <= best["index"] < _shape_count(sp) and sp.sp_get_binned_shape(ctx.ctx) == best
+        seav, ldca = ctx.sketch_image(0)
+        assert not seav.any() and not ldca.any()                           # the tuner left router 0 empty
+        ctx.update(dev(torch, pairs))
+        osk = O.Sketch(oracle_params(kw)).update(pairs)
+        assert_same_sketch(ctx, osk)
+        got, n, rc = ctx.detect()
+        assert_same_results(got, osk.detect()[0])
+    with sp.SuperPoint(**dict(kw, k_log2=12, lc_log2=14)) as ctx:            # k > 1024: no binned scan
+        with pytest.raises(sp.SPError) as e:
+            sp.sp_autotune_binned(ctx.ctx, dev(torch, pairs[:1000]))
+        assert e.value.code == sp.SP_ERR_STATE
