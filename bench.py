@@ -246,7 +246,13 @@ def run_ours(args):
     ctx = sp.SuperPoint(params, stream=stream)
     c = ctx.ctx
     # the binned scan's staging shape, tuned on a sample of the window
-    shape = sp.sp_autotune_binned(c, dev_pairs[: 2 << 24]) if args.scan_mode != 1 else None
+    shape = None
+    if args.scan_mode != 1:
+        if args.shape < 0:
+            shape = sp.sp_autotune_binned(c, dev_pairs[: 2 << 24])
+        else:
+            sp.sp_set_binned_shape(c, args.shape)
+            shape = sp.sp_get_binned_shape(c)
 
     def step():
         sp.sp_reset(c, 0)
@@ -390,7 +396,9 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_extra:
         legs = {"distributed": distributed_leg(torch, sp, W, 24, 64, steps=5, warmup=3),
                 "sliding": sliding_leg(torch, sp, W, 28, passes=1, warmup=1),
-                "serving": serving_leg(torch, sp, W, requests=400, runs=3, warmup=1)}
+                "serving": serving_leg(torch, sp, W, requests=400, runs=3, warmup=1),
+                "detect_many_results": detect_many_leg(torch, sp),
+                "bounds": bounds_leg(torch)}
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -720,6 +728,83 @@ def serving_leg(torch, sp, W, requests=400, runs=3, warmup=1, window_slices=1):
             "clocks": clk}
 
 
+def detect_many_leg(torch, sp, n_hosts=150000, reps=50):
+    """Detection with many results: n_hosts hosts of 64 distinct peers each at
+    theta = 32 (about n_hosts super points, so the result sort spans runs of
+    8,192 keys merged across the grid); detect p50/p99 over reps detects."""
+    rng = np.random.default_rng(51)
+    hosts = rng.permutation(np.unique(rng.integers(0, 2**32, n_hosts + n_hosts // 4, dtype=np.uint32))[:n_hosts])
+    pairs = np.stack([np.repeat(hosts, 64), rng.integers(0, 2**32, hosts.size * 64, dtype=np.uint32)], 1)
+    stream = torch.cuda.current_stream()
+    ctx = sp.SuperPoint(sp.make_params(r=16, isb=(0, 8), ibn=(9, 9), theta=32, seed=51), stream=stream)
+    sp.sp_update(ctx.ctx, 0, torch.from_numpy(np.ascontiguousarray(pairs).reshape(-1).view(np.int32)).cuda())
+    evs = []
+    for _ in range(reps + 3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sp.sp_detect_async(ctx.ctx, 0, 0)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    n_found = sp.sp_results(ctx.ctx)[1]
+    ctx.close()
+    return {"workload": f"{n_hosts} hosts x 64 distinct peers, theta 32, r = 16, SR = 2",
+            "super_points": int(n_found), "detect_latency_ms": _pcts([a.elapsed_time(b) for a, b in evs[3:]])}
+
+
+def bounds_leg(torch, reps=10):
+    """The hardware rates that bound the scan (include/sp_bounds.h), measured
+    on this GPU: streaming reads of 1 GiB (HBM), random 32-bit atomic ORs
+    into a 32 MiB array (L2-resident, as the LDCA of the direct scan) and into
+    a 32 KiB shared-memory array per block (as a bit plane of the binned
+    scan), with the pair rates they allow at LR = 4 bit sets per pair."""
+    import ctypes
+    from paper_1901_07306_gb300 import build as B
+    lib = ctypes.CDLL(B.BOUNDS_LIB)
+    for name in ("sp_probe_stream_read", "sp_probe_l2_red", "sp_probe_smem_atomic"):
+        getattr(lib, name).restype = ctypes.c_int
+    vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+    lib.sp_probe_stream_read.argtypes = [vp, u64, vp, u32, vp]
+    lib.sp_probe_l2_red.argtypes = [vp, u32, u32, u32, u32, vp]
+    lib.sp_probe_smem_atomic.argtypes = [vp, u32, u32, u32, u32, vp]
+    stream = torch.cuda.current_stream()
+    h = ctypes.c_void_p(stream.cuda_stream)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    buf = torch.zeros(1 << 30, dtype=torch.uint8, device="cuda")
+    sink = torch.zeros(1 << 16, dtype=torch.int32, device="cuda")
+    words = torch.zeros(1 << 23, dtype=torch.int32, device="cuda")
+
+    def timed(call):
+        for _ in range(3):
+            assert call() == 0
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            call()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps * 1e-3
+
+    t_read = timed(lambda: lib.sp_probe_stream_read(buf.data_ptr(), buf.numel(), sink.data_ptr(), 0, h))
+    red_ops = 256
+    t_red = timed(lambda: lib.sp_probe_l2_red(words.data_ptr(), 23, red_ops, 0, 7, h))
+    smem_ops = 1024
+    t_smem = timed(lambda: lib.sp_probe_smem_atomic(sink.data_ptr(), 13, smem_ops, 0, 7, h))
+    del buf, words
+    read_gbs = (1 << 30) / t_read / 1e9
+    red_rate = sms * 8 * 256 * red_ops / t_red
+    smem_rate = sms * 4 * 512 * smem_ops / t_smem
+    peak, _ = measured_peak_hbm()
+    return {"hbm_stream_read_gbs": read_gbs,
+            "l2_random_red_or_per_s": red_rate,
+            "smem_random_atomic_or_per_s": smem_rate,
+            "pairs_per_s_if_bound_by": {"hbm_read_8B_per_pair": read_gbs * 1e9 / 8,
+                                        "l2_red_4_per_pair": red_rate / 4,
+                                        "smem_atomic_4_per_pair": smem_rate / 4},
+            "as_frac_of_hbm_roofline": {"l2_red_4_per_pair": red_rate / 4 * 8 / (peak * 1e9),
+                                        "smem_atomic_4_per_pair": smem_rate / 4 * 8 / (peak * 1e9)}}
+
+
 def _line(leg, args, value, ms):
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
@@ -740,6 +825,16 @@ def run_sliding(args):
     leg = sliding_leg(torch, sp, W, args.slide_total_log2, max(1, min(args.steps, 5)), args.warmup,
                       checkpoints=(31, 64, 127))
     print(json.dumps(_line(leg, args, leg["value"], leg["ms_per_pass"])), flush=True)
+    return 0
+
+
+def run_bounds(args):
+    torch, sp, W = _device_setup()
+    clocks = ClockSampler(_gpu_index())
+    clocks.start()
+    leg = bounds_leg(torch)
+    print(json.dumps({"metric": "hardware rates bounding the scan", "unit": "see keys", "n_gpus": 1,
+                      "clocks": clocks.stop(), **leg}), flush=True)
     return 0
 
 
@@ -767,8 +862,10 @@ def main(argv=None):
     ap.add_argument("--ref-budget", type=float, default=60.0)
     ap.add_argument("--pairs-log2", type=int, default=26, help="window size (profiling captures use less)")
     ap.add_argument("--scan-mode", type=int, default=0, help="0 auto, 1 direct (L2 RED), 2 binned")
+    ap.add_argument("--shape", type=int, default=-1,
+                    help="staging shape of the binned scan (sp_binned_shapes index); -1 = autotune on the window")
     ap.add_argument("--workload", default="core_link",
-                    choices=["core_link", "distributed", "sliding", "serving"])
+                    choices=["core_link", "distributed", "sliding", "serving", "bounds"])
     ap.add_argument("--router-log2", type=int, default=24)
     ap.add_argument("--batches-per-router", type=int, default=64)
     ap.add_argument("--slide-total-log2", type=int, default=28)
@@ -783,6 +880,8 @@ def main(argv=None):
         return run_sliding(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "bounds":
+        return run_bounds(args)
     return run_ours(args)
 
 

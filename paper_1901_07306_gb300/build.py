@@ -1,9 +1,10 @@
-"""Builds libsuperpoint.so in-tree with nvcc for sm_103a (GB300).
+"""Builds libsuperpoint.so and libspbounds.so in-tree with nvcc for sm_103a (GB300).
 
 Each translation unit of csrc/ is compiled in parallel to an object under
-_build/, then linked into paper_1901_07306_gb300/libsuperpoint.so.  The CUDA
-runtime is linked statically; the library exports only the C ABI of
-include/superpoint.h.
+_build/, then linked into paper_1901_07306_gb300/libsuperpoint.so (the C ABI
+of include/superpoint.h); bounds/ holds the hardware probes of
+include/sp_bounds.h, linked into paper_1901_07306_gb300/libspbounds.so.  The
+CUDA runtime is linked statically.
 """
 from __future__ import annotations
 
@@ -16,8 +17,10 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
+BOUNDS = os.path.join(HERE, "bounds")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsuperpoint.so")
+BOUNDS_LIB = os.path.join(HERE, "libspbounds.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-fvisibility=hidden",
                      "-Xptxas", "-v"]
@@ -34,15 +37,20 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def _bounds_sources():
+    return sorted(glob.glob(os.path.join(BOUNDS, "*.cu")))
+
+
 def _deps():
-    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.h"))) + [
-        os.path.join(os.path.dirname(HERE), "include", "superpoint.h"), os.path.abspath(__file__)]
+    inc = os.path.join(os.path.dirname(HERE), "include")
+    return (_sources() + _bounds_sources() + sorted(glob.glob(os.path.join(CSRC, "*.h"))) +
+            sorted(glob.glob(os.path.join(inc, "*.h"))) + [os.path.abspath(__file__)])
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(BOUNDS_LIB)):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(BOUNDS_LIB))
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
@@ -51,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    srcs = _sources()
+    srcs = _sources() + _bounds_sources()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
@@ -66,9 +74,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True, capture_output=not verbose)
-    os.replace(tmp, LIB)
+    n_main = len(_sources())
+    for lib, parts in ((LIB, objs[:n_main]), (BOUNDS_LIB, objs[n_main:])):
+        tmp = lib + f".{os.getpid()}.tmp"
+        subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *parts], check=True, capture_output=not verbose)
+        os.replace(tmp, lib)
     if verbose:
         for log in sorted(glob.glob(os.path.join(BUILD, "*.log"))):
             sys.stdout.write(open(log).read())

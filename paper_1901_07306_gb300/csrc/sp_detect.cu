@@ -18,10 +18,20 @@
 //      form of Est >= threshold (Eq. 4).  A full queue falls back to the
 //      same test in one lane.
 //   Survivors are appended as (ip << 32 | z0) keys with one atomic per hit.
-// k_sort_emit: one block sorts the keys (bitonic, in shared memory when they
-//   fit, else in global memory) and writes sp_candidate records with
-//   est taken from a per-context table of -k ln(z0 / k).
+// k_sort_emit: sorts the keys by ip (ascending; ips are unique) and writes
+//   sp_candidate records with est taken from a table of -k ln(z0 / k).  Up to
+//   8,192 keys one block sorts them in shared memory (bitonic).  Above that,
+//   the cooperative grid sorts runs of 8,192 keys in shared memory, one block
+//   per run, then merges pairs of runs in log2(runs) rounds between grid-wide
+//   barriers: each key's place in the merged run is its index in its own run
+//   plus the number of keys of the sibling run below it (binary search).
+//   The rounds alternate between the key buffer and the record buffer (which
+//   holds at least as many bytes), ending in the key buffer.
+#include <cooperative_groups.h>
+
 #include "sp_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace sp {
 
@@ -279,22 +289,8 @@ __device__ __forceinline__ void emit_record(uint64_t key, const double* est_tabl
   *out = c;
 }
 
-__global__ void __launch_bounds__(kSortThreads)
-k_sort_emit(uint64_t* keys, uint32_t cap, const DetectStatus* status, const double* est_table,
-            sp_candidate* out) {
-  extern __shared__ uint64_t s_keys[];
-  const uint32_t n = min(status->count, cap);
-  if (n == 0) return;
-  uint32_t m = 1;
-  while (m < n) m <<= 1;
-  const bool in_smem = m <= kSmemSortCap;
-  uint64_t* a = in_smem ? s_keys : keys;   // global buffer holds a power of two >= cap
-  for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-    if (in_smem) a[i] = i < n ? keys[i] : ~0ull;
-    else if (i >= n) a[i] = ~0ull;
-  }
-  __syncthreads();
-  // bitonic sort, ascending
+// bitonic sort of m (a power of two, <= kSmemSortCap) keys in shared memory, ascending
+__device__ void smem_bitonic(uint64_t* a, uint32_t m) {
   for (uint32_t size = 2; size <= m; size <<= 1) {
     for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
       for (uint32_t i = threadIdx.x; i < m / 2; i += blockDim.x) {
@@ -304,11 +300,84 @@ k_sort_emit(uint64_t* keys, uint32_t cap, const DetectStatus* status, const doub
         const uint64_t x = a[lo], y = a[hi];
         if ((x > y) == up) { a[lo] = y; a[hi] = x; }
       }
-      if (!in_smem) __threadfence_block();
       __syncthreads();
     }
   }
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) emit_record(a[i], est_table, out + i);
+}
+
+// number of keys of run[0, len) below key (the keys of a run are sorted and unique)
+__device__ __forceinline__ uint32_t count_below(const uint64_t* run, uint32_t len, uint64_t key) {
+  uint32_t lo = 0, hi = len;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (run[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_emit(uint64_t* keys, uint32_t cap, const DetectStatus* status, const double* est_table,
+            sp_candidate* out) {
+  extern __shared__ uint64_t s_keys[];
+  const uint32_t n = min(status->count, cap);        // the same for every block
+  if (n == 0) return;
+  if (n <= kSmemSortCap) {                          // one block, in shared memory
+    if (blockIdx.x != 0) return;
+    uint32_t m = 1;
+    while (m < n) m <<= 1;
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) s_keys[i] = i < n ? keys[i] : ~0ull;
+    __syncthreads();
+    smem_bitonic(s_keys, m);
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) emit_record(s_keys[i], est_table, out + i);
+    return;
+  }
+  cg::grid_group grid = cg::this_grid();
+  // 1. runs of kSmemSortCap keys, sorted in shared memory, written back in place
+  const uint32_t runs = (n + kSmemSortCap - 1) / kSmemSortCap;
+  for (uint32_t r = blockIdx.x; r < runs; r += gridDim.x) {
+    const uint32_t base = r * kSmemSortCap;
+    const uint32_t len = min(kSmemSortCap, n - base);
+    for (uint32_t i = threadIdx.x; i < kSmemSortCap; i += blockDim.x) s_keys[i] = i < len ? keys[base + i] : ~0ull;
+    __syncthreads();
+    smem_bitonic(s_keys, kSmemSortCap);
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) keys[base + i] = s_keys[i];
+    __syncthreads();
+  }
+  // 2. merge rounds; an odd number of rounds starts with a copy so that the
+  // last round writes the key buffer
+  uint32_t rounds = 0;
+  for (uint64_t w = kSmemSortCap; w < n; w <<= 1) ++rounds;
+  uint64_t* tmp = reinterpret_cast<uint64_t*>(out);  // cap records of 24 bytes hold n keys
+  uint64_t* src = keys;
+  uint64_t* dst = tmp;
+  const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t gsize = (uint64_t)gridDim.x * blockDim.x;
+  grid.sync();
+  if (rounds & 1u) {
+    for (uint64_t i = gtid; i < n; i += gsize) tmp[i] = keys[i];
+    src = tmp;
+    dst = keys;
+    grid.sync();
+  }
+  for (uint64_t w = kSmemSortCap; w < n; w <<= 1) {
+    for (uint64_t i = gtid; i < n; i += gsize) {
+      const uint64_t base = i / (2 * w) * (2 * w);
+      const uint64_t mid = base + w < n ? base + w : n;
+      const uint64_t end = base + 2 * w < n ? base + 2 * w : n;
+      const uint64_t key = src[i];
+      uint64_t pos;
+      if (i < mid) pos = i + count_below(src + mid, (uint32_t)(end - mid), key);          // run A
+      else pos = (i - mid) + base + count_below(src + base, (uint32_t)(mid - base), key);  // run B
+      dst[pos] = key;
+    }
+    grid.sync();
+    uint64_t* t = src;
+    src = dst;
+    dst = t;
+  }
+  // 3. records (src is the key buffer now)
+  for (uint64_t i = gtid; i < n; i += gsize) emit_record(src[i], est_table, out + i);
 }
 
 }  // namespace
@@ -339,7 +408,19 @@ cudaError_t launch_sort_emit(uint64_t* keys, uint32_t cap, const DetectStatus* s
   const size_t smem = kSmemSortCap * sizeof(uint64_t);
   cudaError_t e = cudaFuncSetAttribute(k_sort_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_sort_emit<<<1, kSortThreads, smem, s>>>(keys, cap, status, est_table, out);
+  // a cooperative grid (every block resident) of at most one block per SM,
+  // and no more blocks than runs of the largest count
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_emit, kSortThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const uint32_t max_runs = (cap + kSmemSortCap - 1) / kSmemSortCap;
+  const unsigned grid = (unsigned)(max_runs < (uint32_t)sms ? (max_runs ? max_runs : 1u) : (uint32_t)sms);
+  void* args[] = {&keys, &cap, &status, &est_table, &out};
+  e = cudaLaunchCooperativeKernel((const void*)k_sort_emit, dim3(grid), dim3(kSortThreads), args, smem, s);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

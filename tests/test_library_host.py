@@ -116,3 +116,17 @@ def test_ldca_sizing_matches_lemma1_and_theorem1(sp):
         assert lr * 2 ** c <= budget
     with pytest.raises(sp.SPError):
         sp.sp_size_ldca(0, 10, 1 << 16)
+
+
+def test_bounds_probe_library_exports_its_header():
+    """libspbounds.so (the hardware probes behind the roofline figures) loads
+    without a GPU and exports exactly what include/sp_bounds.h declares."""
+    import ctypes
+    from paper_1901_07306_gb300 import build
+    build.build()
+    text = open(os.path.join(ROOT, "include", "sp_bounds.h")).read()
+    names = sorted(set(re.findall(r"^SPB_API [\w\s\*]+?\b(sp_\w+)\(", text, flags=re.M)))
+    assert names == ["sp_probe_l2_red", "sp_probe_smem_atomic", "sp_probe_stream_read"]
+    lib = ctypes.CDLL(build.BOUNDS_LIB)
+    for name in names:
+        assert hasattr(lib, name), name

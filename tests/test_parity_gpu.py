@@ -387,3 +387,33 @@ def test_autotune_binned_picks_a_shape_and_stays_exact(sp, torch):
         with pytest.raises(sp.SPError) as e:
             sp.sp_autotune_binned(ctx.ctx, dev(torch, pairs[:1000]))
         assert e.value.code == sp.SP_ERR_STATE
+
+
+def _many_hosts(n_hosts, seed):
+    """n_hosts hosts with 64 distinct peers each, shuffled: at theta = 32 each
+    is a super point, so the detection returns about n_hosts results."""
+    rng = np.random.default_rng(seed)
+    hosts = np.unique(rng.integers(0, 2**32, n_hosts + n_hosts // 4 + 64, dtype=np.uint32))[:n_hosts]
+    hosts = rng.permutation(hosts)
+    pairs = np.stack([np.repeat(hosts, 64), rng.integers(0, 2**32, hosts.size * 64, dtype=np.uint32)], 1)
+    return np.ascontiguousarray(pairs[rng.permutation(pairs.shape[0])]), hosts
+
+
+@pytest.mark.parametrize("n_hosts", [12000, 20000, 150000])
+def test_detect_sort_beyond_one_block(sp, torch, n_hosts):
+    """More results than one block sorts in shared memory (8,192): runs of
+    8,192 sorted per block, then merged across the grid (one round, two
+    rounds, five rounds at more than 65,536 results); the list equals the
+    oracle's, in order, bit for bit."""
+    kw = dict(r=16, isb=(0, 8), ibn=(9, 9), theta=32, seed=51)
+    pairs, hosts = _many_hosts(n_hosts, 51 + n_hosts)
+    with sp.SuperPoint(**kw) as ctx:
+        ctx.update(dev(torch, pairs))
+        got, n, rc = ctx.detect()
+        osk = O.Sketch(oracle_params(kw)).update(pairs)
+        want, n_want, overflow = osk.detect()
+        assert not overflow and rc == sp.SP_OK and n == n_want > 8192
+        assert_same_results(got, want)
+        if n_hosts > 65536:
+            assert n > 65536
+            assert len(set(hosts.tolist()) - set(got["ip"].tolist())) <= n_hosts // 100
