@@ -92,10 +92,9 @@ __device__ __forceinline__ void st_chunk(uint32_t* dst, uint4 a, uint4 b) {
 //      shared atomic and stores the hip there (a row that is full sends the
 //      pair to L2 REDs instead);
 //   2. (after every TPR tiles) each thread takes bins tid, tid + THREADS, ...:
-//      it moves the row's
-//      whole 8-hip chunks to the bin's list with 32-byte stores and keeps the
-//      remainder (< 8 hips) at the front of the row; the queued pairs set
-//      their SEAV bits.
+//      it moves the row's whole 8-hip chunks to the bin's list with 32-byte
+//      stores and keeps the remainder (< 8 hips) at the front of the row; the
+//      queued pairs set their SEAV bits, taken by consecutive threads.
 // At the end the remainders go to the lists with plain stores; an appending
 // launch first takes the tail of a list that is not a whole chunk back into
 // the row, so lists stay dense and chunk stores stay 32-byte aligned.
@@ -271,7 +270,7 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
       const uint32_t f = s_fill[b];
       if (f >= (uint32_t)kChunk) flush_row(b, f < (uint32_t)STAGE ? f : (uint32_t)STAGE);
     }
-    for (uint32_t e = (tid & 31u) * (THREADS / 32u) + (tid >> 5); e < qn; e += THREADS) {   // a bijection on [0, THREADS)
+    for (uint32_t e = tid; e < qn; e += THREADS) {   // consecutive threads: the fewest warps
       const uint2 x = s_queue[e];
       seav_set(d, seav, x.x, x.y);
     }
@@ -320,34 +319,51 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
   }
 }
 
-template <int LR, int THREADS>
+// k_apply, LCL = log2 LC when it is fixed at compile time (profiles D, D3
+// and S: constant shifts and row offsets), 0 for any LC.
+template <int LR, int THREADS, int LCL>
 __global__ void __launch_bounds__(THREADS)
 k_apply(DevParams d, const uint32_t* __restrict__ lists, const uint32_t* __restrict__ counts,
         uint32_t G, uint32_t cap, uint32_t* __restrict__ planes, bool accumulate) {
   extern __shared__ uint32_t s_plane[];
   const uint32_t b = blockIdx.x;
-  const uint32_t words = ((uint32_t)LR << d.lc_log2) >> 5;       // plane words
+  const uint32_t lc_log2 = LCL ? (uint32_t)LCL : d.lc_log2;
+  const uint32_t words = ((uint32_t)LR << lc_log2) >> 5;          // plane words
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t nwarps = THREADS / 32;
   // LH_i(hip) = h >> cshift (5 <= lc_log2 <= 20): LDC h >> cshift of row i is
   // bit (h >> cshift) mod 32 of plane word (i << (lc_log2 - 5)) + (h >> (cshift + 5))
-  const uint32_t cshift = 32u - d.lc_log2;
-  const uint32_t row_words_log2 = d.lc_log2 - 5u;
+  const uint32_t cshift = 32u - lc_log2;
+  const uint32_t row_words_log2 = lc_log2 - 5u;
   // accumulator layout [ceil(words / 8)][k][8]: word w of plane b at
   // (w / 8) k 8 + 8 b + w mod 8, so that a 32-byte chunk holds 8 words of one plane
   const uint64_t chunk_stride = (uint64_t)(1u << d.k_log2) * 8u;
   uint32_t* dst = planes + (uint64_t)b * 8u;
   auto at_word = [&](uint32_t w) { return dst + (uint64_t)(w >> 3) * chunk_stride + (w & 7u); };
+  // the rows' hash words, held in registers
+  uint32_t a_lo[LR], a_hi[LR];
+  uint64_t bw[LR];
+#pragma unroll
+  for (int r = 0; r < LR; ++r) {
+    a_lo[r] = (uint32_t)d.ha[2 + r];
+    a_hi[r] = (uint32_t)(d.ha[2 + r] >> 32);
+    bw[r] = d.hb[2 + r];
+  }
   for (uint32_t w = tid; w < words; w += THREADS) s_plane[w] = accumulate ? *at_word(w) : 0u;
   __syncthreads();
   auto set_bits = [&](uint32_t hip) {
 #pragma unroll
     for (int r = 0; r < LR; ++r) {
-      const uint32_t h = mas(d.ha[2 + r], d.hb[2 + r], hip);
-      // the clamping funnel shift gives 0 for the shift of 32 at lc_log2 = 5;
-      // the wrapping one takes the bit position mod 32
-      atomicOr(&s_plane[((uint32_t)r << row_words_log2) + __funnelshift_rc(h, 0u, cshift + 5u)],
-               __funnelshift_l(0u, 1u, h >> cshift));
+      const uint64_t lo = (uint64_t)a_lo[r] * hip + bw[r];
+      const uint32_t h = (uint32_t)(lo >> 32) + a_hi[r] * hip;      // MAS (Sec. 3.3 LH_r)
+      if (LCL) {
+        atomicOr(&s_plane[((uint32_t)r << row_words_log2) + (h >> (cshift + 5u))], 1u << ((h >> cshift) & 31u));
+      } else {
+        // the clamping funnel shift gives 0 for the shift of 32 at lc_log2 = 5;
+        // the wrapping one takes the bit position mod 32
+        atomicOr(&s_plane[((uint32_t)r << row_words_log2) + __funnelshift_rc(h, 0u, cshift + 5u)],
+                 __funnelshift_l(0u, 1u, h >> cshift));
+      }
     }
   };
   for (uint32_t c = warp; c < G; c += nwarps) {
@@ -492,22 +508,33 @@ cudaError_t bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const B
   return cudaGetLastError();
 }
 
-template <int LR, int THREADS>
+template <int LR, int THREADS, int LCL>
 cudaError_t apply_round_t(const DevParams& d, const BinnedScratch& s, uint32_t cap, bool accumulate, cudaStream_t st) {
   const uint32_t bins = 1u << d.k_log2;
   const uint32_t words = ((uint32_t)LR << d.lc_log2) >> 5;
   const size_t apply_smem = (size_t)words * sizeof(uint32_t);
-  cudaError_t e = cudaFuncSetAttribute(k_apply<LR, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)apply_smem);
+  auto kern = k_apply<LR, THREADS, LCL>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_smem);
   if (e != cudaSuccess) return e;
-  k_apply<LR, THREADS><<<bins, THREADS, apply_smem, st>>>(d, s.lists, s.counts, s.ctas, cap, s.planes, accumulate);
+  kern<<<bins, THREADS, apply_smem, st>>>(d, s.lists, s.counts, s.ctas, cap, s.planes, accumulate);
   return cudaGetLastError();
+}
+
+template <int LR, int THREADS>
+cudaError_t apply_round_lc(const DevParams& d, const BinnedScratch& s, uint32_t cap, bool accumulate,
+                           cudaStream_t st) {
+  if (LR == 4) {                      // the profiles' LDCA widths get constant shifts
+    if (d.lc_log2 == 16) return apply_round_t<LR, THREADS, 16>(d, s, cap, accumulate, st);
+    if (d.lc_log2 == 18) return apply_round_t<LR, THREADS, 18>(d, s, cap, accumulate, st);
+    if (d.lc_log2 == 14) return apply_round_t<LR, THREADS, 14>(d, s, cap, accumulate, st);
+  }
+  return apply_round_t<LR, THREADS, 0>(d, s, cap, accumulate, st);
 }
 
 template <int LR>
 cudaError_t apply_round(const DevParams& d, const BinnedScratch& s, uint32_t cap, bool accumulate, cudaStream_t st) {
-  return s.shape.apply_threads == 256 ? apply_round_t<LR, 256>(d, s, cap, accumulate, st)
-                                      : apply_round_t<LR, 512>(d, s, cap, accumulate, st);
+  return s.shape.apply_threads == 256 ? apply_round_lc<LR, 256>(d, s, cap, accumulate, st)
+                                      : apply_round_lc<LR, 512>(d, s, cap, accumulate, st);
 }
 
 }  // namespace
@@ -522,10 +549,9 @@ bool binned_applicable(const DevParams& d) {
 // flush's 16-byte row reads of 8 consecutive bins hit all 32 banks; a row
 // holds the < 8 hips a flush leaves plus a round's arrivals with headroom
 // (one block per SM: 2 tiles of 8K pairs, 16 per bin on average, 44-hip rows;
-// two per SM: 1 tile of 4K pairs, 20-hip rows).
+// two per SM: 2 tiles of 4K pairs, 20-hip rows).
 constexpr BinShape kShapes[] = {
   {1024, 44, 2, 1, 512}, {1024, 44, 2, 1, 256},
-  {512, 20, 1, 2, 512},  {512, 20, 1, 2, 256},
   {512, 20, 2, 2, 512},  {512, 20, 2, 2, 256},
 };
 
@@ -579,7 +605,6 @@ cudaError_t binned_bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, 
   // to L2 REDs, so a smaller cap only costs speed)
   if (cap > s.cap_alloc) cap = s.cap_alloc;
   const BinShape& h = s.shape;
-  if (h.threads == 512 && h.tpr == 1) return bin_chunk<512, 20, 1, 2>(d, seav, ldca, src, s, cap, append, rot, st);
   if (h.threads == 512) return bin_chunk<512, 20, 2, 2>(d, seav, ldca, src, s, cap, append, rot, st);
   return bin_chunk<1024, 44, 2, 1>(d, seav, ldca, src, s, cap, append, rot, st);
 }
