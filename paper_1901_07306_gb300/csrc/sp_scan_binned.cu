@@ -276,32 +276,39 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
     }
     __syncthreads();
   };
-  // Tiles in pairs (i, i + 1): the two register buffers alternate, and each
-  // tile's loads go out before the work on the tile before it; a flush round
-  // after every TPR tiles.
+  // Tiles in pairs (i, i + 1) in the two register buffers.  A buffer's loads
+  // for tile t + 2 go out as soon as tile t is staged, so the flush round
+  // runs with both next tiles in flight (the flush's stores and the stream's
+  // loads overlap); a flush round after every TPR tiles.
   uint4 ra[kVec], rb[kVec];
   TileRef ta{nullptr, 0u, false}, tb{nullptr, 0u, false};
   if (tile_of(0) < n_tiles) {
     ta = tile_ref(tile_of(0));
     if (ta.vec) load_tile(ra, ta.p);
   }
+  if (tile_of(1) < n_tiles) {
+    tb = tile_ref(tile_of(1));
+    if (tb.vec) load_tile(rb, tb.p);
+  }
   uint32_t par = 0;
   for (uint64_t i = 0; tile_of(i) < n_tiles; i += 2) {
     const bool has_b = tile_of(i + 1) < n_tiles;
-    if (has_b) {
-      tb = tile_ref(tile_of(i + 1));
-      if (tb.vec) load_tile(rb, tb.p);
-    }
     stage_tile(ra, ta, par);
-    if (TPR == 1) {
-      flush_round(par);
-      par ^= 1u;
-    }
     if (tile_of(i + 2) < n_tiles) {
       ta = tile_ref(tile_of(i + 2));
       if (ta.vec) load_tile(ra, ta.p);
     }
-    if (has_b) stage_tile(rb, tb, par);
+    if (TPR == 1) {
+      flush_round(par);
+      par ^= 1u;
+    }
+    if (has_b) {
+      stage_tile(rb, tb, par);
+      if (tile_of(i + 3) < n_tiles) {
+        tb = tile_ref(tile_of(i + 3));
+        if (tb.vec) load_tile(rb, tb.p);
+      }
+    }
     flush_round(par);
     par ^= 1u;
   }
