@@ -67,20 +67,24 @@ def scan_source_hash():
 
 
 def scan_traffic_from_profile(n_pairs):
-    """DRAM bytes (read + write) of one scan stage over n_pairs, scaled from
-    the committed ncu summary of a smaller case (traffic grows in proportion
-    to the pairs); None when the scan sources changed since that capture."""
-    path = os.path.join(ROOT, "profiles", "scan_core_link_2e25.md")
-    try:
-        text = open(path).read()
+    """DRAM bytes (read + write) of one scan stage (k_bin + k_apply) over
+    n_pairs, scaled from the committed one-kernel ncu summaries of a smaller
+    case (traffic grows in proportion to the pairs); None when the scan
+    sources changed since those captures."""
+    total = 0.0
+    for kernel in ("k_bin", "k_apply"):
+        path = os.path.join(ROOT, "profiles", f"{kernel}_core_link_2e25.md")
+        try:
+            text = open(path).read()
+        except OSError:
+            return None
         m_sha = re.search(r"scan_sources_sha256_16:\s*([0-9a-f]{16})", text)
-        m_b = re.search(r"stage_dram_bytes:\s*([0-9]+)", text)
-        m_n = re.search(r"stage_pairs:\s*([0-9]+)", text)
-        if m_sha and m_b and m_n and m_sha.group(1) == scan_source_hash():
-            return int(int(m_b.group(1)) * n_pairs / int(m_n.group(1)))
-    except Exception:
-        pass
-    return None
+        m_b = re.search(r"kernel_dram_bytes:\s*([0-9]+)", text)
+        m_n = re.search(r"kernel_pairs:\s*([0-9]+)", text)
+        if not (m_sha and m_b and m_n) or m_sha.group(1) != scan_source_hash():
+            return None
+        total += int(m_b.group(1)) * n_pairs / int(m_n.group(1))
+    return int(total)
 
 
 def launches_per_step(n_pairs, scan_mode):
@@ -666,6 +670,50 @@ def sliding_leg(torch, sp, W, total_log2=28, passes=2, warmup=1, checkpoints=())
            "n_pairs": total, "slices": len(slices), "window_slices": k, "passes": passes,
            "value": total / (ms * 1e-3), "unit": UNIT, "ms_per_pass": ms,
            "detect_latency_ms": _pcts(det), "super_points_last_window": int(n_found), "clocks": clk}
+    # the per-slice step as one CUDA graph (slide + scan through a one-entry
+    # device batch table + detect), recorded once and replayed per slice with
+    # the table entry copied in from a device array of all slices' entries
+    entries = np.zeros(len(slices), sp.BATCH)
+    for t, x in enumerate(dev_slices):
+        entries[t] = (x.data_ptr(), slices[t].shape[0], 0, 0)
+    dev_entries = torch.from_numpy(entries.view(np.uint8)).cuda().view(len(slices), -1)
+    table = torch.empty_like(dev_entries[0])
+    g = torch.cuda.CUDAGraph()
+
+    def graph_pass():
+        sp.sp_reset(c, 0)
+        table.copy_(dev_entries[0])
+        sp.sp_update_batched_device(c, table, 1)
+        sp.sp_detect_async(c, 0, 1024)
+        for t in range(1, len(slices)):
+            table.copy_(dev_entries[t])
+            g.replay()
+
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):                     # warm up the captured calls off the capture
+        sp.sp_set_stream(c, side)
+        sp.sp_slide(c, 0)
+        sp.sp_update_batched_device(c, table, 1)
+        sp.sp_detect_async(c, 0, 1024)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        sp.sp_set_stream(c, torch.cuda.current_stream())
+        sp.sp_slide(c, 0)
+        sp.sp_update_batched_device(c, table, 1)
+        sp.sp_detect_async(c, 0, 1024)
+    sp.sp_set_stream(c, stream)
+    graph_pass()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(passes):
+        graph_pass()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_g = a.elapsed_time(b) / passes
+    out["graph"] = {"value": total / (ms_g * 1e-3), "unit": UNIT, "ms_per_pass": ms_g,
+                    "form": "per slice one CUDA graph replay: slide + scan (device batch table, direct form) + detect",
+                    "super_points_last_window": int(sp.sp_results(c)[1])}
     if checkpoints:
         one_pass(keep=set(checkpoints))
         out["accuracy"] = {str(t): accuracy(found[t], exact_super_points(

@@ -381,8 +381,13 @@ SP_API int sp_results_device(sp_ctx* ctx, const sp_candidate** dev_records, cons
  * inactive ("0") for detect, merge and export.  Each call also sweeps one of
  * 255 - window_slices segments of the router's stamps (the per-slice counter
  * maintenance of Sec. 5.2), so a call costs 1/(255 - k) of a pass over them.
- * Async.  In a discrete context (window_slices = 1) it equals sp_reset.
- * Errors: SP_ERR_ROUTER. */
+ * The slice clock t lives in device memory and the kernels read it there, so
+ * the per-slice step -- sp_slide, sp_update_batched_device on a table the
+ * caller rewrites, sp_detect_async -- can be recorded once in a CUDA graph
+ * and replayed slice after slice (each replay advances t).  The library's
+ * host-side count of sp_slide calls (sp_merge's same-slice check) does not
+ * see replays.  Async.  In a discrete context (window_slices = 1) it equals
+ * sp_reset.  Errors: SP_ERR_ROUTER. */
 SP_API int sp_slide(sp_ctx* ctx, uint32_t router);
 
 /* Checkpoint / WP->GS shipment (Sec. 4.2): a self-describing image of one

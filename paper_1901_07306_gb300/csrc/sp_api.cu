@@ -119,7 +119,7 @@ struct sp_ctx {
   uint8_t* stamps = nullptr;                // n_routers * st_stride bytes
   uint8_t* window = nullptr;                // n_routers * stride: the window's bits, rebuilt per read
   uint64_t st_seav_pad = 0, st_stride = 0;
-  uint64_t* slice = nullptr;                // current slice t of each router
+  uint64_t* slice = nullptr;                // host count of sp_slide calls per router (merge's same-slice check)
 
   // batched scan: a ring of batch tables (pinned host copy, device copy), so
   // the host waits only for the upload issued kTableRing calls earlier
@@ -139,7 +139,8 @@ struct sp_ctx {
 
   uint8_t* st_seav(uint32_t router) const { return stamps + (uint64_t)router * st_stride; }
   uint8_t* st_ldca(uint32_t router) const { return stamps + (uint64_t)router * st_stride + st_seav_pad; }
-  uint32_t slice_id(uint32_t router) const { return (uint32_t)(slice[router] % 255u) + 1u; }
+  uint64_t* clock = nullptr;                // device: slice counter t of each router (the kernels' clock)
+  uint64_t* dev_clock(uint32_t router) const { return clock + router; }
   // SEAV as 32-bit words (the padding past seav_bytes is zero in every region)
   uint64_t seav_words() const { return (seav_bytes + 3) / 4; }
 
@@ -331,6 +332,7 @@ void sp_destroy(sp_ctx* ctx) {
   }
   free(ctx->planes_dirty);
   free(ctx->slice);
+  cudaFree(ctx->clock);
   free(ctx->slice_dirty);
   if (ctx->result_host) cudaFreeHost(ctx->result_host);
   for (auto& t : ctx->tables) {
@@ -435,8 +437,10 @@ int sp_create(const sp_params* p, void* cuda_stream, sp_ctx** out) {
     c->st_seav_pad = align_up(c->seav_bytes * 8, kAlign);
     c->st_stride = c->st_seav_pad + align_up(c->ldca_bytes * 8, kAlign);
     if (cudaMalloc(&c->stamps, c->st_stride * p->n_routers) != cudaSuccess ||
-        cudaMalloc(&c->window, c->stride * p->n_routers) != cudaSuccess) { cudaGetLastError(); rc = SP_ERR_NOMEM; }
-    else if (sp::launch_zero(c->stamps, c->st_stride * p->n_routers, c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
+        cudaMalloc(&c->window, c->stride * p->n_routers) != cudaSuccess ||
+        cudaMalloc(&c->clock, sizeof(uint64_t) * p->n_routers) != cudaSuccess) { cudaGetLastError(); rc = SP_ERR_NOMEM; }
+    else if (sp::launch_zero(c->stamps, c->st_stride * p->n_routers, c->stream) != cudaSuccess ||
+             cudaMemsetAsync(c->clock, 0, sizeof(uint64_t) * p->n_routers, c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
   }
   if (rc == SP_OK) rc = wait_stream(c);
   if (rc != SP_OK) {
@@ -558,7 +562,7 @@ static int commit(sp_ctx* ctx, uint32_t router) {
   int rc = fold_router(ctx, router);
   if (rc != SP_OK || !ctx->slice_dirty[router]) return rc;
   if (sp::launch_commit(reinterpret_cast<uint32_t*>(ctx->seav(router)), ctx->st_seav(router), ctx->seav_words(),
-                        ctx->ldca(router), ctx->st_ldca(router), ctx->ldca_bytes / 4, ctx->slice_id(router),
+                        ctx->ldca(router), ctx->st_ldca(router), ctx->ldca_bytes / 4, ctx->dev_clock(router),
                         ctx->stream) != cudaSuccess)
     return SP_ERR_CUDA;
   ctx->slice_dirty[router] = false;
@@ -573,7 +577,7 @@ static int commit_window(sp_ctx* ctx, uint32_t router) {
   if (sp::launch_commit_window(reinterpret_cast<uint32_t*>(ctx->seav(router)), ctx->st_seav(router),
                                ctx->seav_words(), ctx->ldca(router), ctx->st_ldca(router), ctx->ldca_bytes / 4,
                                reinterpret_cast<uint32_t*>(ctx->wseav(router)), ctx->wldca(router),
-                               ctx->slice_id(router), ctx->p.window_slices, ctx->stream) != cudaSuccess)
+                               ctx->dev_clock(router), ctx->p.window_slices, ctx->stream) != cudaSuccess)
     return SP_ERR_CUDA;
   ctx->slice_dirty[router] = false;
   return SP_OK;
@@ -586,6 +590,7 @@ int sp_reset(sp_ctx* ctx, uint32_t router) {
   ctx->slice_dirty[router] = false;
   if (ctx->sliding) {
     ctx->slice[router] = 0;
+    if (cudaMemsetAsync(ctx->dev_clock(router), 0, sizeof(uint64_t), ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
     if (sp::launch_zero(ctx->st_seav(router), ctx->st_stride, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
   }
   return sp::launch_zero(ctx->seav(router), ctx->stride, ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
@@ -929,7 +934,7 @@ int sp_merge(sp_ctx* ctx, const uint32_t* routers, uint32_t n, uint32_t dst_rout
       if (routers[i] != dst_router && ms < 4096) ssrc[ms++] = ctx->st_seav(routers[i]);
     }
     if (rc != SP_OK) return rc;
-    return sp::launch_merge_stamp(ctx->st_seav(dst_router), ssrc, ms, ctx->st_stride, ctx->slice_id(dst_router),
+    return sp::launch_merge_stamp(ctx->st_seav(dst_router), ssrc, ms, ctx->st_stride, ctx->dev_clock(dst_router),
                                   ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
   }
   int rc = fold_router(ctx, dst_router);
@@ -1072,13 +1077,11 @@ int sp_slide(sp_ctx* ctx, uint32_t router) {
   int rc = commit(ctx, router);                       // slice t's bits carry id(t)
   if (rc != SP_OK) return rc;
   ctx->slice[router] += 1;
-  // sweep segment (t mod M) of the router's counters, M = 255 - k
-  const uint64_t M = 255u - ctx->p.window_slices;
-  const uint64_t units = ctx->st_stride / 16;
-  const uint64_t seg = ctx->slice[router] % M;
-  const uint64_t lo = units * seg / M * 16, hi = units * (seg + 1) / M * 16;
-  return sp::launch_clean(ctx->st_seav(router) + lo, 0, hi - lo, ctx->slice_id(router), ctx->p.window_slices,
-                          ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+  // t += 1 on the device, then the sweep of segment (t mod M), M = 255 - k,
+  // of the router's counters: every argument is fixed, so a graph that
+  // recorded this call advances the window at each replay
+  return sp::launch_tick_clean(ctx->st_seav(router), ctx->st_stride, ctx->dev_clock(router), ctx->p.window_slices,
+                               ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
 }
 
 int sp_export(sp_ctx* ctx, uint32_t router, void* host_buf, uint64_t cap, uint64_t* n) {

@@ -122,17 +122,19 @@ cudaError_t launch_scan_binned(const DevParams& d, uint8_t* seav, uint32_t* ldca
 // ldca |= transpose(planes)
 cudaError_t launch_fold(const DevParams& d, const uint32_t* planes, uint32_t* ldca, int grid, cudaStream_t st);
 // sliding window (sp_slide.cu); a sketch region is nw 32-bit words, word i
-// owning the 32 stamps [32 i, 32 i + 32) of its stamp region
-// stamps id on the counters of the slice sketch's set bits, then clears the sketch
+// owning the 32 stamps [32 i, 32 i + 32) of its stamp region; `clock` is the
+// router's slice counter t in device memory (slice id t mod 255 + 1)
+// stamps id(t) on the counters of the slice sketch's set bits, then clears the sketch
 cudaError_t launch_commit(uint32_t* seav, uint8_t* st_seav, uint64_t seav_words, uint32_t* ldca,
-                          uint8_t* st_ldca, uint64_t ldca_words, uint32_t id, cudaStream_t s);
+                          uint8_t* st_ldca, uint64_t ldca_words, const uint64_t* clock, cudaStream_t s);
 // launch_commit, and the window's bits (active stamps) into wseav / wldca
 cudaError_t launch_commit_window(uint32_t* seav, uint8_t* st_seav, uint64_t seav_words, uint32_t* ldca,
                                  uint8_t* st_ldca, uint64_t ldca_words, uint32_t* wseav, uint32_t* wldca,
-                                 uint32_t id, uint32_t k, cudaStream_t s);
-cudaError_t launch_clean(uint8_t* stamps, uint64_t lo, uint64_t hi, uint32_t cur, uint32_t k, cudaStream_t s);
+                                 const uint64_t* clock, uint32_t k, cudaStream_t s);
+// t += 1, then the sweep of segment (t mod (255 - k)) of the router's stamps[0, bytes)
+cudaError_t launch_tick_clean(uint8_t* stamps, uint64_t bytes, uint64_t* clock, uint32_t k, cudaStream_t s);
 cudaError_t launch_merge_stamp(uint8_t* dst, const uint8_t* const* srcs, uint32_t n_src, uint64_t bytes,
-                               uint32_t cur, cudaStream_t s);
+                               const uint64_t* clock, cudaStream_t s);
 cudaError_t launch_merge(uint8_t* dst, const uint8_t* const* srcs, uint32_t n_src,
                          uint64_t bytes, cudaStream_t s);
 cudaError_t launch_detect(const DevParams& d, const uint8_t* seav, const uint32_t* ldca,

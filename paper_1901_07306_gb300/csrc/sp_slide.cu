@@ -27,6 +27,11 @@
 //                 maintenance of Sec. 5.2, spread over slices).
 //   k_merge_stamp keeps, per counter, the youngest stamp over the routers
 //                 (the OR of Sec. 4.2 for counters of a common slice clock).
+//   k_tick        advances a router's slice clock by one.
+// Every router's slice clock t lives in device memory and the kernels read
+// it there, so the launches of a slice (slide, scan, detect) take the same
+// arguments at every slice and can be recorded once in a CUDA graph and
+// replayed slice after slice.
 #include "sp_internal.h"
 
 namespace sp {
@@ -34,6 +39,9 @@ namespace sp {
 namespace {
 
 constexpr int kThreads = 256;
+
+// id(t) = t mod 255 + 1 of the slice clock t
+__device__ __forceinline__ uint32_t slice_id(const uint64_t* clock) { return (uint32_t)(*clock % 255u) + 1u; }
 
 __device__ __forceinline__ uint32_t age_of(uint32_t stamp, uint32_t cur) {
   return cur >= stamp ? cur - stamp : cur + 255u - stamp;
@@ -54,9 +62,13 @@ __device__ __forceinline__ uint32_t active4(uint32_t s, uint32_t cur4, uint32_t 
   return (((active_mask4(s, cur4, k4) & 0x01010101u) * 0x00204081u) >> 21) & 0xFu;
 }
 
-// stamps[lo, hi): reset those of age >= k (16 per uint4)
+// Segment (t mod M) of a router's stamps, M = 255 - k, of units16 16-byte
+// units: reset those of age >= k (16 per uint4).
 __global__ void __launch_bounds__(kThreads)
-k_clean(uint4* __restrict__ st, uint64_t lo16, uint64_t hi16, uint32_t cur, uint32_t k) {
+k_clean(uint4* __restrict__ st, uint64_t units16, const uint64_t* __restrict__ clock, uint32_t k) {
+  const uint64_t t = *clock, M = 255u - k, seg = t % M;
+  const uint64_t lo16 = units16 * seg / M, hi16 = units16 * (seg + 1) / M;
+  const uint32_t cur = (uint32_t)(t % 255u) + 1u;
   const uint32_t cur4 = cur * 0x01010101u, k4 = k * 0x01010101u;
   for (uint64_t i = lo16 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi16;
        i += (uint64_t)gridDim.x * blockDim.x) {
@@ -99,8 +111,9 @@ __device__ __forceinline__ void store8(uint4* st, uint64_t i, const uint32_t (&v
 // router start a fresh slice sketch.  Zero words cost one 4-byte read.
 __global__ void __launch_bounds__(kThreads)
 k_commit(uint32_t* __restrict__ seav, uint4* __restrict__ st_seav, uint64_t seav_words,
-         uint32_t* __restrict__ ldca, uint4* __restrict__ st_ldca, uint64_t ldca_words, uint32_t id) {
-  const uint32_t id4 = id * 0x01010101u;
+         uint32_t* __restrict__ ldca, uint4* __restrict__ st_ldca, uint64_t ldca_words,
+         const uint64_t* __restrict__ clock) {
+  const uint32_t id4 = slice_id(clock) * 0x01010101u;
   const uint64_t n = seav_words + ldca_words;
   for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x) {
     const bool in_seav = j < seav_words;
@@ -124,8 +137,9 @@ k_commit(uint32_t* __restrict__ seav, uint4* __restrict__ st_seav, uint64_t seav
 __global__ void __launch_bounds__(kThreads)
 k_commit_window(uint32_t* __restrict__ seav, uint4* __restrict__ st_seav, uint64_t seav_words,
                 uint32_t* __restrict__ ldca, uint4* __restrict__ st_ldca, uint64_t ldca_words,
-                uint32_t* __restrict__ wseav, uint32_t* __restrict__ wldca, uint32_t id, uint32_t k) {
-  const uint32_t id4 = id * 0x01010101u, k4 = k * 0x01010101u;   // k <= 128 < 256
+                uint32_t* __restrict__ wseav, uint32_t* __restrict__ wldca, const uint64_t* __restrict__ clock,
+                uint32_t k) {
+  const uint32_t id4 = slice_id(clock) * 0x01010101u, k4 = k * 0x01010101u;   // k <= 128 < 256
   const uint64_t n = seav_words + ldca_words;
   for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x) {
     const bool in_seav = j < seav_words;
@@ -154,9 +168,11 @@ struct StampSrc {
   const uint4* p[32];
 };
 
-// dst = youngest stamp over dst and the sources (all at slice id `cur`)
+// dst = youngest stamp over dst and the sources (all at dst's slice clock)
 __global__ void __launch_bounds__(kThreads)
-k_merge_stamp(uint4* __restrict__ dst, StampSrc src, uint32_t n_src, uint64_t n16, uint32_t cur) {
+k_merge_stamp(uint4* __restrict__ dst, StampSrc src, uint32_t n_src, uint64_t n16,
+              const uint64_t* __restrict__ clock) {
+  const uint32_t cur = slice_id(clock);
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (uint64_t)gridDim.x * blockDim.x) {
     uint4 a = dst[i];
     uint32_t w[4] = {a.x, a.y, a.z, a.w};
@@ -182,6 +198,8 @@ k_merge_stamp(uint4* __restrict__ dst, StampSrc src, uint32_t n_src, uint64_t n1
   }
 }
 
+__global__ void k_tick(uint64_t* clock) { *clock += 1u; }
+
 int grid_cap() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -200,36 +218,39 @@ unsigned grid_for(uint64_t work) {
 }  // namespace
 
 cudaError_t launch_commit(uint32_t* seav, uint8_t* st_seav, uint64_t seav_words, uint32_t* ldca,
-                          uint8_t* st_ldca, uint64_t ldca_words, uint32_t id, cudaStream_t s) {
+                          uint8_t* st_ldca, uint64_t ldca_words, const uint64_t* clock, cudaStream_t s) {
   k_commit<<<grid_for(seav_words + ldca_words), kThreads, 0, s>>>(
-      seav, reinterpret_cast<uint4*>(st_seav), seav_words, ldca, reinterpret_cast<uint4*>(st_ldca), ldca_words, id);
+      seav, reinterpret_cast<uint4*>(st_seav), seav_words, ldca, reinterpret_cast<uint4*>(st_ldca), ldca_words,
+      clock);
   return cudaGetLastError();
 }
 
 cudaError_t launch_commit_window(uint32_t* seav, uint8_t* st_seav, uint64_t seav_words, uint32_t* ldca,
                                  uint8_t* st_ldca, uint64_t ldca_words, uint32_t* wseav, uint32_t* wldca,
-                                 uint32_t id, uint32_t k, cudaStream_t s) {
+                                 const uint64_t* clock, uint32_t k, cudaStream_t s) {
   k_commit_window<<<grid_for(seav_words + ldca_words), kThreads, 0, s>>>(
       seav, reinterpret_cast<uint4*>(st_seav), seav_words, ldca, reinterpret_cast<uint4*>(st_ldca), ldca_words,
-      wseav, wldca, id, k);
+      wseav, wldca, clock, k);
   return cudaGetLastError();
 }
 
-cudaError_t launch_clean(uint8_t* stamps, uint64_t lo, uint64_t hi, uint32_t cur, uint32_t k, cudaStream_t s) {
-  const uint64_t lo16 = lo / 16, hi16 = hi / 16;
-  if (hi16 <= lo16) return cudaSuccess;
-  k_clean<<<grid_for(hi16 - lo16), kThreads, 0, s>>>(reinterpret_cast<uint4*>(stamps), lo16, hi16, cur, k);
+cudaError_t launch_tick_clean(uint8_t* stamps, uint64_t bytes, uint64_t* clock, uint32_t k, cudaStream_t s) {
+  k_tick<<<1, 1, 0, s>>>(clock);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const uint64_t units16 = bytes / 16, M = 255u - k;
+  k_clean<<<grid_for(units16 / M + 1), kThreads, 0, s>>>(reinterpret_cast<uint4*>(stamps), units16, clock, k);
   return cudaGetLastError();
 }
 
 cudaError_t launch_merge_stamp(uint8_t* dst, const uint8_t* const* srcs, uint32_t n_src, uint64_t bytes,
-                               uint32_t cur, cudaStream_t s) {
+                               const uint64_t* clock, cudaStream_t s) {
   const uint64_t n16 = bytes / 16;
   for (uint32_t base = 0; base < n_src; base += 32) {
     StampSrc l{};
     const uint32_t m = (n_src - base) < 32u ? (n_src - base) : 32u;
     for (uint32_t j = 0; j < m; ++j) l.p[j] = reinterpret_cast<const uint4*>(srcs[base + j]);
-    k_merge_stamp<<<grid_for(n16), kThreads, 0, s>>>(reinterpret_cast<uint4*>(dst), l, m, n16, cur);
+    k_merge_stamp<<<grid_for(n16), kThreads, 0, s>>>(reinterpret_cast<uint4*>(dst), l, m, n16, clock);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -295,7 +295,11 @@ class SketchServer:
                 window, window_pairs, window_reqs = window + 1, 0, []
                 progressed = True
             if not progressed:
-                time.sleep(20e-6)
+                if steps or detects:
+                    time.sleep(0)                                     # device work in flight: yield, poll again
+                elif pending:
+                    time.sleep(min(1e-3, max(0.0, pending[0].arrival - now())))   # until the next arrival
+
         ops.synchronize()
         self.elapsed = now()
         return self.windows

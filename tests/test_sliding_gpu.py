@@ -196,3 +196,60 @@ def test_every_update_form_mid_slice_reads(sp, torch, scan_mode):
             assert same_sketch(ctx, O.sliding_window_sketch(op, whole, t, k)), t
             assert same_sketch(ctx, O.Sketch(op), router=1), t     # router 1 never received pairs
         torch.cuda.synchronize()
+
+
+def test_per_slice_cuda_graph_replay(sp, torch):
+    """Sec. 5 per-slice step recorded once as a CUDA graph -- slide, scan of
+    the slice through a one-entry device batch table, detect -- and replayed
+    slice after slice with the table rewritten: the slice clock lives on the
+    device, so every replay advances the window, and the window's sketch and
+    results equal the oracle's at every slice (past the window length, so
+    slices also leave it)."""
+    sizes = np.random.default_rng(71).integers(2000, 20000, 12)
+    slices, sp_hosts, sched = W.sliding_stream(seed=71, sizes=sizes, n_sp=6, sp_degree_per_slice=(100, 400),
+                                               n_background=3000)
+    k = 4
+    kw = dict(theta=256, seed=71, window_slices=k)
+    op = oparams(kw)
+    pool = [dev(torch, x) for x in slices]
+    table = torch.zeros(sp.BATCH.itemsize, dtype=torch.uint8, device="cuda")
+
+    def write_table(t):
+        rec = np.zeros(1, sp.BATCH)
+        rec[0] = (pool[t].data_ptr(), slices[t].shape[0], 0, 0)
+        table.copy_(torch.from_numpy(rec.view(np.uint8)))
+
+    def check(ctx, t):
+        torch.cuda.synchronize()
+        osk = O.sliding_window_sketch(op, slices, t, k)
+        assert same_sketch(ctx, osk), t
+        got, n, rc = sp.sp_results(ctx.ctx)
+        want, n_want, _ = osk.detect()
+        assert n == n_want and np.array_equal(got["ip"], want["ip"]) and np.array_equal(got["z0"], want["z0"]), t
+
+    with sp.SuperPoint(**kw) as ctx:
+        c = ctx.ctx
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):                    # slices 0 and 1 without a graph
+            sp.sp_set_stream(c, side)
+            for t in (0, 1):
+                if t:
+                    sp.sp_slide(c, 0)
+                write_table(t)
+                sp.sp_update_batched_device(c, table, 1)
+                sp.sp_detect_async(c, 0, 0)
+        torch.cuda.synchronize()
+        sp.sp_set_stream(c, torch.cuda.current_stream())
+        check(ctx, 1)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            sp.sp_set_stream(c, torch.cuda.current_stream())
+            sp.sp_slide(c, 0)
+            sp.sp_update_batched_device(c, table, 1)
+            sp.sp_detect_async(c, 0, 0)
+        sp.sp_set_stream(c, torch.cuda.current_stream())
+        for t in range(2, len(slices)):
+            write_table(t)
+            g.replay()
+            check(ctx, t)
