@@ -21,7 +21,8 @@ Workloads (the paper measured CAIDA OC192 traces, which these stand in for):
     population (30% shared sources); 1,000 global super points whose peers
     are split evenly so that no single router sees theta of them.
   * ``sliding_stream``    -- time slices of lognormal size, super points
-    switching on and off per slice (for the sliding-window extension).
+    switching on and off per slice, background hosts one per 64 pairs of the
+    stream (for the sliding-window extension).
   * ``uniform_pairs``     -- i.i.d. uniform pairs for small tests.
 """
 from __future__ import annotations
@@ -218,7 +219,10 @@ def sliding_stream(seed: int = 4, sizes: np.ndarray | None = None, n_sp: int = 6
     rng = np.random.default_rng(seed)
     sizes = slice_sizes(seed) if sizes is None else np.asarray(sizes)
     n_slices = sizes.size
-    n_background = n_background or max(1024, int(sizes.mean() // 16))
+    # background hosts as dense as on the core link: one per 64 pairs of the
+    # stream (4M at 2^28 pairs), so a 32-slice window of 2^26 pairs gives each
+    # about 16 pairs
+    n_background = n_background or max(1024, int(sizes.sum() // 64))
     hosts = _distinct_hosts(rng, n_background)
     sp_hosts = _distinct_hosts(rng, n_sp, exclude=hosts)
     schedule = np.zeros((n_sp, n_slices), bool)
