@@ -581,8 +581,7 @@ def distributed_leg(torch, sp, W, router_log2=24, batches_per_router=64, steps=1
     rlist, tlist = [r for r, _ in batches], [t for _, t in batches]
 
     def step(batched):
-        for r in range(n_routers + 1):
-            sp.sp_reset(c, r)
+        sp.sp_reset_range(c, 0, n_routers + 1)
         if batched:
             sp.sp_update_batched(c, rlist, tlist)
         else:

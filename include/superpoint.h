@@ -204,6 +204,12 @@ SP_API int sp_get_params(const sp_ctx* ctx, sp_params* out);
  * In a sliding context it also forgets every slice.  Errors: SP_ERR_ROUTER. */
 SP_API int sp_reset(sp_ctx* ctx, uint32_t router);
 
+/* sp_reset for routers first .. first + count - 1 (a new discrete window for
+ * every watch point at once, Sec. 3): their sketches are contiguous, so one
+ * zeroing launch covers them.  Async.  Errors: SP_ERR_ROUTER (range outside
+ * the context). */
+SP_API int sp_reset_range(sp_ctx* ctx, uint32_t first, uint32_t count);
+
 /* Scan (Sec. 3.1-3.3, Sec. 4.1): for every pair of dev_pairs[0 .. 2 n_pairs),
  * sets bit H2(oip) of the SE at Idx(i, LP(hip)) in every row i of SEA RP(hip)
  * when lsb(H1(oip)) >= tau, and bit H3(oip) of LDC LH_i(hip) in every LDCA

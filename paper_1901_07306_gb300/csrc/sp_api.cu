@@ -596,6 +596,25 @@ int sp_reset(sp_ctx* ctx, uint32_t router) {
   return sp::launch_zero(ctx->seav(router), ctx->stride, ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
 }
 
+int sp_reset_range(sp_ctx* ctx, uint32_t first, uint32_t count) {
+  if (!ctx) return SP_ERR_PARAM;
+  if (count == 0) return SP_OK;
+  if (first >= ctx->p.n_routers || count > ctx->p.n_routers - first) return SP_ERR_ROUTER;
+  if (ctx->sliding) {                            // stamps and clocks are per router
+    for (uint32_t r = first; r < first + count; ++r) {
+      const int rc = sp_reset(ctx, r);
+      if (rc != SP_OK) return rc;
+    }
+    return SP_OK;
+  }
+  for (uint32_t r = first; r < first + count; ++r) {
+    ctx->planes_dirty[r] = false;                // pending planes belong to the old window
+    ctx->slice_dirty[r] = false;
+  }
+  // the routers' regions are contiguous: one zeroing launch for all of them
+  return sp::launch_zero(ctx->seav(first), ctx->stride * count, ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+}
+
 int sp_update(sp_ctx* ctx, uint32_t router, const uint32_t* dev_pairs, uint64_t n_pairs) {
   if (!ctx) return SP_ERR_PARAM;
   if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;

@@ -172,11 +172,11 @@ class GpuOps:
             out_t = torch.from_numpy(out.view(np.uint8)).pin_memory()
             status = torch.zeros(2, dtype=torch.int32).pin_memory()
             sp.sp_results_async(c, out_t, self.report_cap, status)
-            for r in range(self.n_routers + 1):
-                if self.window_slices > 1:
+            if self.window_slices > 1:
+                for r in range(self.n_routers + 1):
                     sp.sp_slide(c, r)
-                else:
-                    sp.sp_reset(c, r)
+            else:
+                sp.sp_reset_range(c, 0, self.n_routers + 1)           # every router and the global one, one launch
             ev = torch.cuda.Event()
             ev.record(self.compute)
         return ev, (out_t, status)

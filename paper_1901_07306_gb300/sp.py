@@ -43,6 +43,7 @@ EXPORTED = (
     "sp_export", "sp_import", "sp_detect_noalloc", "sp_update_batched_device", "sp_autotune",
     "sp_results_async", "sp_psu", "sp_size_ldca", "sp_set_timeout", "sp_copy_sketch", "sp_merge_device",
     "sp_binned_shapes", "sp_set_binned_shape", "sp_get_binned_shape", "sp_autotune_binned",
+    "sp_reset_range",
 )
 
 
@@ -106,6 +107,7 @@ def _load():
         "sp_set_timeout": (i32, [vp, u32]),
         "sp_get_params": (i32, [vp, P(sp_params)]),
         "sp_reset": (i32, [vp, u32]),
+        "sp_reset_range": (i32, [vp, u32, u32]),
         "sp_update": (i32, [vp, u32, vp, u64]),
         "sp_update_host": (i32, [vp, u32, vp, u64]),
         "sp_update_batched": (i32, [vp, u32, P(u32), P(vp), P(u64)]),
@@ -236,6 +238,10 @@ def sp_get_params(ctx: int) -> sp_params:
 
 def sp_reset(ctx: int, router: int = 0) -> None:
     _check(lib.sp_reset(ctypes.c_void_p(ctx), router), "sp_reset")
+
+
+def sp_reset_range(ctx: int, first: int, count: int) -> None:
+    _check(lib.sp_reset_range(ctypes.c_void_p(ctx), first, count), "sp_reset_range")
 
 
 def _pairs_ptr(pairs):

@@ -417,3 +417,26 @@ def test_detect_sort_beyond_one_block(sp, torch, n_hosts):
         if n_hosts > 65536:
             assert n > 65536
             assert len(set(hosts.tolist()) - set(got["ip"].tolist())) <= n_hosts // 100
+
+
+def test_reset_range(sp, torch):
+    """sp_reset_range zeroes exactly the routers of the range (one launch),
+    drops their pending binned planes, and leaves the others intact."""
+    kw = dict(theta=256, seed=61, n_routers=4, scan_mode=2)
+    op = oracle_params(kw)
+    data = [W.uniform_pairs(50000 + 1000 * r, seed=610 + r, n_hosts=5000) for r in range(4)]
+    with sp.SuperPoint(**kw) as ctx:
+        for r in range(4):
+            ctx.update(dev(torch, data[r]), router=r)
+        sp.sp_reset_range(ctx.ctx, 1, 2)
+        for r in range(4):
+            seav, ldca = ctx.sketch_image(r)
+            if r in (1, 2):
+                assert not seav.any() and not ldca.any(), r
+            else:
+                assert_same_sketch(ctx, O.Sketch(op).update(data[r]), router=r)
+        ctx.update(dev(torch, data[0]), router=2)               # the router works on after the reset
+        assert_same_sketch(ctx, O.Sketch(op).update(data[0]), router=2)
+        with pytest.raises(sp.SPError) as e:
+            sp.sp_reset_range(ctx.ctx, 3, 2)
+        assert e.value.code == sp.SP_ERR_ROUTER
