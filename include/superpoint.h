@@ -251,6 +251,22 @@ typedef struct sp_batch {
 SP_API int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
                              const uint32_t* const* dev_pairs, const uint64_t* n_pairs);
 
+/* Batched scan of batches in host memory (the serving path of many watch
+ * points, Sec. 4.1): copies batch b (host_pairs[b], n_pairs[b] pairs; pinned
+ * memory makes the copies asynchronous) into dev_arena -- caller-owned device
+ * memory of arena_bytes, 16-byte aligned; the batches are packed in order,
+ * each at a 16-byte boundary -- on copy_stream (a cudaStream_t, NULL = the
+ * legacy default stream), makes the context's stream wait for the copies, and
+ * scans them as sp_update_batched does.  One call per engine step, the copy
+ * loop in C.  The caller orders copy_stream after the last scan that read the
+ * arena, and keeps the host buffers and the arena alive until the stream has
+ * passed the scan.  Async.  Errors: SP_ERR_PARAM (NULL or misaligned arena,
+ * the batches do not fit it), SP_ERR_ROUTER, SP_ERR_STATE (inside a stream
+ * capture), SP_ERR_CUDA. */
+SP_API int sp_update_batched_host(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
+                                  const uint32_t* const* host_pairs, const uint64_t* n_pairs, void* dev_arena,
+                                  uint64_t arena_bytes, void* copy_stream);
+
 /* Batched scan over a table that already lives in device memory
  * (dev_batches[0 .. n_batches), n_batches <= 8192), always by the one
  * persistent launch (direct form).  The kernel reads sizes and pointers when it

@@ -97,6 +97,7 @@ struct sp_ctx {
   uint32_t cap = 0;
   uint32_t timeout_ms = kDefaultTimeoutMs;  // 0: waits are unbounded
   cudaEvent_t ev_wait = nullptr;            // marks the stream's work for a bounded wait
+  cudaEvent_t ev_arena = nullptr;           // sp_update_batched_host: the copies into the arena are done
   bool detect_issued = false;
   uint32_t last_threshold = 0;
   // results: status, error word and the first kResultPrefix records land in
@@ -351,6 +352,7 @@ void sp_destroy(sp_ctx* ctx) {
   cudaFree(ctx->kerr);
   cudaFree(ctx->est_table);
   if (ctx->ev_wait) cudaEventDestroy(ctx->ev_wait);
+  if (ctx->ev_arena) cudaEventDestroy(ctx->ev_arena);
   delete ctx;
 }
 
@@ -810,6 +812,33 @@ int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
   int rc = upload_table(ctx, rest.data(), (uint32_t)rest.size(), &dev_tab);
   if (rc != SP_OK) return rc;
   return launch_table(ctx, dev_tab, (uint32_t)rest.size());
+}
+
+int sp_update_batched_host(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
+                           const uint32_t* const* host_pairs, const uint64_t* n_pairs, void* dev_arena,
+                           uint64_t arena_bytes, void* copy_stream) {
+  if (!ctx) return SP_ERR_PARAM;
+  if (n_batches == 0) return SP_OK;
+  if (!routers || !host_pairs || !n_pairs || !dev_arena || ((uintptr_t)dev_arena & 15u)) return SP_ERR_PARAM;
+  // the batches' places in the arena: packed, each at a 16-byte boundary
+  std::vector<const uint32_t*> dev(n_batches);
+  uint64_t off = 0;
+  for (uint32_t b = 0; b < n_batches; ++b) {
+    if (routers[b] >= ctx->p.n_routers) return SP_ERR_ROUTER;
+    if (n_pairs[b] && !host_pairs[b]) return SP_ERR_PARAM;
+    dev[b] = reinterpret_cast<const uint32_t*>(static_cast<uint8_t*>(dev_arena) + off);
+    off += align_up(n_pairs[b] * 8, 16);
+    if (off > arena_bytes) return SP_ERR_PARAM;
+  }
+  if (!ctx->ev_arena && cudaEventCreateWithFlags(&ctx->ev_arena, cudaEventDisableTiming) != cudaSuccess)
+    return SP_ERR_CUDA;
+  cudaStream_t cs = static_cast<cudaStream_t>(copy_stream);
+  for (uint32_t b = 0; b < n_batches; ++b)
+    if (n_pairs[b] && cudaMemcpyAsync(const_cast<uint32_t*>(dev[b]), host_pairs[b], n_pairs[b] * 8,
+                                      cudaMemcpyHostToDevice, cs) != cudaSuccess) return SP_ERR_CUDA;
+  if (cudaEventRecord(ctx->ev_arena, cs) != cudaSuccess || cudaStreamWaitEvent(ctx->stream, ctx->ev_arena, 0) != cudaSuccess)
+    return SP_ERR_CUDA;
+  return sp_update_batched(ctx, n_batches, routers, dev.data(), n_pairs);
 }
 
 int sp_update_batched_device(sp_ctx* ctx, const sp_batch* dev_batches, uint32_t n_batches) {

@@ -133,23 +133,18 @@ class GpuOps:
         return not self.batched or self.arena_free[arena] is None or self.arena_free[arena].query()
 
     def issue_step(self, step: list, arena: int, offsets: list):
-        """Copies the step's requests into the arena (at the given word
-        offsets) and scans them with one batched call (batched engine), or
-        copies and scans each on its own (plain path).  Returns the event
-        that completes with the step's scan."""
+        """Copies the step's requests into the arena and scans them with one
+        batched call (batched engine: sp_update_batched_host, which packs the
+        requests at the word offsets the engine computed -- 16-byte
+        boundaries -- and runs the copy loop in C), or copies and scans each
+        on its own (plain path).  Returns the event that completes with the
+        step's scan."""
         sp, c = self.sp, self.ctx.ctx
         if self.batched:
-            bufs = [self.arenas[arena][o:o + r.pairs.numel()] for r, o in zip(step, offsets)]
-            with torch.cuda.stream(self.copy):
-                if self.arena_free[arena] is not None:
-                    self.copy.wait_event(self.arena_free[arena])
-                for r, b in zip(step, bufs):
-                    b.copy_(r.pairs, non_blocking=True)
-                copied = torch.cuda.Event()
-                copied.record(self.copy)
-            self.compute.wait_event(copied)
-            with torch.cuda.stream(self.compute):
-                sp.sp_update_batched(c, [r.router for r in step], bufs)
+            if self.arena_free[arena] is not None:
+                self.copy.wait_event(self.arena_free[arena])      # the last scan that read this arena
+            sp.sp_update_batched_host(c, [r.router for r in step], [r.pairs for r in step], self.arenas[arena],
+                                      self.copy)
         else:
             with torch.cuda.stream(self.compute):
                 for r in step:                                # one copy + one launch each
@@ -266,7 +261,7 @@ class SketchServer:
                     and self.budget.fits(pending[0].nbytes):
                 r = pending[0]
                 if self.batched:
-                    words = r.pairs.numel()
+                    words = (r.pairs.numel() + 3) // 4 * 4                # packed at 16-byte boundaries
                     if words > arena_words:
                         raise ValueError(f"a {r.nbytes}-byte request exceeds half the staging budget")
                     if used + words > arena_words:

@@ -43,7 +43,7 @@ EXPORTED = (
     "sp_export", "sp_import", "sp_detect_noalloc", "sp_update_batched_device", "sp_autotune",
     "sp_results_async", "sp_psu", "sp_size_ldca", "sp_set_timeout", "sp_copy_sketch", "sp_merge_device",
     "sp_binned_shapes", "sp_set_binned_shape", "sp_get_binned_shape", "sp_autotune_binned",
-    "sp_reset_range",
+    "sp_reset_range", "sp_update_batched_host",
 )
 
 
@@ -111,6 +111,7 @@ def _load():
         "sp_update": (i32, [vp, u32, vp, u64]),
         "sp_update_host": (i32, [vp, u32, vp, u64]),
         "sp_update_batched": (i32, [vp, u32, P(u32), P(vp), P(u64)]),
+        "sp_update_batched_host": (i32, [vp, u32, P(u32), P(vp), P(u64), vp, u64, vp]),
         "sp_merge": (i32, [vp, P(u32), u32, u32]),
         "sp_copy_sketch": (i32, [vp, u32, vp, u64, P(u64)]),
         "sp_merge_device": (i32, [vp, P(vp), u32, u32]),
@@ -276,6 +277,21 @@ def sp_update_batched(ctx: int, routers, batches) -> None:
     for i, b in enumerate(batches):
         ptrs[i], ns[i] = _pairs_ptr(b)
     _check(lib.sp_update_batched(ctypes.c_void_p(ctx), nb, r, ptrs, ns), "sp_update_batched")
+
+
+def sp_update_batched_host(ctx: int, routers, host_batches, dev_arena, copy_stream) -> None:
+    """host_batches: pinned host tensors/arrays of pairs; dev_arena: CUDA
+    tensor the batches are copied into (packed at 16-byte boundaries);
+    copy_stream: the stream the copies run on."""
+    nb = len(host_batches)
+    r = (ctypes.c_uint32 * nb)(*routers)
+    ptrs = (ctypes.c_void_p * nb)()
+    ns = (ctypes.c_uint64 * nb)()
+    for i, b in enumerate(host_batches):
+        ptrs[i], ns[i] = _pairs_ptr(b)
+    _check(lib.sp_update_batched_host(ctypes.c_void_p(ctx), nb, r, ptrs, ns, ctypes.c_void_p(dev_arena.data_ptr()),
+                                      dev_arena.numel() * dev_arena.element_size(),
+                                      ctypes.c_void_p(_stream_handle(copy_stream))), "sp_update_batched_host")
 
 
 def sp_update_batched_device(ctx: int, dev_table, n_batches: int) -> None:

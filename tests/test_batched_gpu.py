@@ -220,3 +220,25 @@ def test_thousands_of_small_batches_of_one_router(sp, torch, n_batches, lo, hi):
         assert rc == sp.SP_OK and n == n_want
         assert np.array_equal(got["ip"], want["ip"]) and np.array_equal(got["z0"], want["z0"])
         assert set(planted.tolist()) <= set(got["ip"].tolist())
+
+
+def test_batched_host_copies_into_arena(sp, torch):
+    """sp_update_batched_host: host batches (pinned, uneven sizes, odd pair
+    counts) copied into a caller arena on a copy stream and scanned in one
+    call; every router's sketch equals the oracle's; an arena too small is
+    refused before anything is copied."""
+    kw = dict(theta=256, seed=18, n_routers=3)
+    routers, data = _batches(18, 3, 30, 3, 15)
+    host = [torch.from_numpy(np.ascontiguousarray(x, np.uint32).reshape(-1).view(np.int32).copy()).pin_memory()
+            for x in data]
+    words = sum((h.numel() + 3) // 4 * 4 for h in host)
+    arena = torch.empty(words, dtype=torch.int32, device="cuda")
+    copy = torch.cuda.Stream()
+    with sp.SuperPoint(**kw) as ctx:
+        with pytest.raises(sp.SPError) as e:
+            sp.sp_update_batched_host(ctx.ctx, routers, host, arena[: words - 4], copy)
+        assert e.value.code == sp.SP_ERR_PARAM
+        sp.sp_update_batched_host(ctx.ctx, routers, host, arena, copy)
+        for r in range(3):
+            mine = [x for rr, x in zip(routers, data) if rr == r]
+            assert same_sketch(ctx, O.Sketch(oparams(kw)).update(np.concatenate(mine)), r), r
