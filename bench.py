@@ -400,7 +400,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_extra:
         legs = {"distributed": distributed_leg(torch, sp, W, 24, 64, steps=5, warmup=3),
                 "sliding": sliding_leg(torch, sp, W, 28, passes=1, warmup=1),
-                "serving": serving_leg(torch, sp, W, requests=400, runs=3, warmup=1),
+                "serving": serving_leg(torch, sp, W, requests=400, runs=5, warmup=1),
                 "detect_many_results": detect_many_leg(torch, sp),
                 "bounds": bounds_leg(torch)}
     if rank != 0:

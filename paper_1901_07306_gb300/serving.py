@@ -34,6 +34,7 @@ window is available on the host.
 """
 from __future__ import annotations
 
+import gc
 import time
 from collections import deque
 from dataclasses import dataclass
@@ -214,7 +215,19 @@ class SketchServer:
     def run(self, requests: list[Request]):
         """Serves the requests (sorted by arrival); returns self.windows.
         Raises ServingTimeout when a step's scan or a window's detection has
-        not completed timeout_s after it was issued."""
+        not completed timeout_s after it was issued.  Python's cyclic garbage
+        collector is paused while the loop runs (a collection can stall the
+        host for tens of milliseconds, a latency spike for every request in
+        flight)."""
+        was_enabled = gc.isenabled()
+        gc.disable()
+        try:
+            return self._run(requests)
+        finally:
+            if was_enabled:
+                gc.enable()
+
+    def _run(self, requests: list[Request]):
         ops = self.ops
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         steps = deque()           # (event, issued at, requests, bytes, step index)
