@@ -107,8 +107,9 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
   constexpr int QUEUE = TPR * TILE / 32;              // sampled pairs per round: 4x the expected 2^-7
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const uint32_t bins = 1u << d.k_log2;                                // <= 1024
-  uint32_t* stage = reinterpret_cast<uint32_t*>(smem_raw);             // [bins][STAGE]
-  uint2* s_queue = reinterpret_cast<uint2*>(stage + bins * STAGE);    // [QUEUE] sampled (hip, h1)
+  uint32_t* stage = reinterpret_cast<uint32_t*>(smem_raw);             // [bins][STAGE], then a 32-word sink
+  uint32_t* sink = stage + bins * STAGE;                                // stores of pairs a full row refused
+  uint2* s_queue = reinterpret_cast<uint2*>(sink + 32);               // [QUEUE] sampled (hip, h1)
   uint32_t* s_fill = reinterpret_cast<uint32_t*>(s_queue + QUEUE);     // [bins] hips in the row
   uint32_t* s_cursor = s_fill + bins;                                   // [bins] list fill (whole chunks)
   __shared__ uint32_t s_qn[2];                                          // queue fill, by tile parity
@@ -118,6 +119,9 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
   const uint32_t slot = (cta + rot) % G;          // which tiles this block takes
   const uint32_t tau_mask = (1u << d.tau) - 1u;
   const uint32_t h3_shift = 32u - d.k_log2;
+  const uint32_t lane = tid & 31u;
+  uint32_t lt_mask;                                // lanes below this one
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt_mask));
   // tiles of the streams, back to back: stream b owns tiles [s_tpref[b], s_tpref[b + 1])
   if (tid == 0) {
     uint64_t acc = 0;
@@ -170,7 +174,6 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
   // stores; a pair whose row is full is marked in the returned mask
   auto stage_group = [&](const uint32_t (&hip)[kGroup], const uint32_t (&oip)[kGroup], uint32_t valid,
                          uint32_t par, uint32_t (&bin)[kGroup]) {
-    const uint32_t lane = tid & 31u;
     uint32_t at[kGroup], over = 0;
 #pragma unroll
     for (int q = 0; q < kGroup; ++q) {
@@ -179,7 +182,7 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
       if (ballot) {
         uint32_t first = 0;
         if (lane == 0) first = atomicAdd(&s_qn[par], (uint32_t)__popc(ballot));
-        first = __shfl_sync(kFull, first, 0) + (uint32_t)__popc(ballot & ((1u << lane) - 1u));
+        first = __shfl_sync(kFull, first, 0) + (uint32_t)__popc(ballot & lt_mask);
         if (((ballot >> lane) & 1u) && first < (uint32_t)QUEUE) s_queue[first] = make_uint2(hip[q], h1);
         else if ((ballot >> lane) & 1u) over |= 1u << (kGroup + q);   // queue full: SEAV bits directly
       }
@@ -190,7 +193,10 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
       at[q] = ((valid >> q) & 1u) ? atomicAdd(&s_fill[bin[q]], 1u) : 0xFFFFu;
 #pragma unroll
     for (int q = 0; q < kGroup; ++q) {
-      if (at[q] < (uint32_t)STAGE) stage[bin[q] * STAGE + at[q]] = hip[q];
+      // no branch: a pair that finds its row full (or no pair) stores to
+      // this lane's sink word instead
+      uint32_t* dst = at[q] < (uint32_t)STAGE ? stage + bin[q] * STAGE + at[q] : sink + lane;
+      *dst = hip[q];
       over |= (at[q] >= (uint32_t)STAGE && at[q] != 0xFFFFu ? 1u : 0u) << q;
     }
     return over;
@@ -507,7 +513,8 @@ cudaError_t bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const B
                       const BinnedScratch& s, uint32_t cap, bool append, uint32_t rot, cudaStream_t st) {
   const uint32_t bins = 1u << d.k_log2;
   // the bins' staging rows, the sampled-pair queue, 2 counters per bin
-  const size_t bin_smem = (size_t)bins * STAGE * 4 + (size_t)(TPR * THREADS * kVec * 2 / 32) * 8 + (size_t)bins * 8;
+  const size_t bin_smem = (size_t)bins * STAGE * 4 + 32 * 4 + (size_t)(TPR * THREADS * kVec * 2 / 32) * 8 +
+                          (size_t)bins * 8;
   auto kern = k_bin<THREADS, STAGE, TPR, PER_SM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
   if (e != cudaSuccess) return e;
