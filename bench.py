@@ -230,6 +230,14 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     else:
         torch.cuda.set_device(0)
+        if args.exchange:                         # the exchange leg on a one-rank NCCL group
+            import socket
+            import torch.distributed as dist
+            with socket.socket() as sock:
+                sock.bind(("127.0.0.1", 0))
+                port = sock.getsockname()[1]
+            dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1,
+                                    device_id=torch.device("cuda", 0))
     from paper_1901_07306_gb300 import build as B
     if rank == 0 or world == 1:
         B.build()
@@ -246,7 +254,8 @@ def run_ours(args):
     dev_pairs = flat.cuda()
     stream = torch.cuda.current_stream()
     # router 1 is the global server of the multi-GPU exchange
-    params = sp.make_params(seed=args.seed, theta=theta, scan_mode=args.scan_mode, n_routers=2 if world > 1 else 1)
+    with_exchange = world > 1 or args.exchange
+    params = sp.make_params(seed=args.seed, theta=theta, scan_mode=args.scan_mode, n_routers=2 if with_exchange else 1)
     ctx = sp.SuperPoint(params, stream=stream)
     c = ctx.ctx
     # the binned scan's staging shape, tuned on a sample of the window
@@ -391,7 +400,7 @@ def run_ours(args):
     # N > 1: the WP -> GS exchange (Sec. 4.2) over NCCL, timed after the
     # headline region: every rank's device sketch all-gathered, ORed into a
     # global router and detected on every rank
-    xchg = exchange_leg(torch, sp, W, c, args, rank, world) if world > 1 else None
+    xchg = exchange_leg(torch, sp, W, c, args, rank, world) if with_exchange else None
     sp.sp_destroy(c)
     ctx.ctx = None
     acc = accuracy(found_ips, exact_super_points(pairs, theta)) if not args.no_extra else None
@@ -440,7 +449,7 @@ def run_ours(args):
         "exchange": xchg,
     }
     print(json.dumps(line), flush=True)
-    if world > 1:
+    if with_exchange:
         torch.distributed.destroy_process_group()
     return 0
 
@@ -902,6 +911,8 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--exchange", action="store_true",
+                    help="run the multi-GPU exchange leg even on one GPU (a one-rank NCCL group)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the accuracy report and the distributed, sliding and serving legs")
     ap.add_argument("--e2e-steps", type=int, default=50)
