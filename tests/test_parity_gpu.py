@@ -383,6 +383,9 @@ def test_autotune_binned_picks_a_shape_and_stays_exact(sp, torch):
         assert_same_sketch(ctx, osk)
         got, n, rc = ctx.detect()
         assert_same_results(got, osk.detect()[0])
+        with pytest.raises(sp.SPError) as e:
+            sp.sp_set_binned_shape(ctx.ctx, _shape_count(sp))
+        assert e.value.code == sp.SP_ERR_PARAM
     with sp.SuperPoint(**dict(kw, k_log2=12, lc_log2=14)) as ctx:            # k > 1024: no binned scan
         with pytest.raises(sp.SPError) as e:
             sp.sp_autotune_binned(ctx.ctx, dev(torch, pairs[:1000]))

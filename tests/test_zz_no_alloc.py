@@ -104,3 +104,24 @@ def test_noalloc_estimate_table_of_each_k(sp, torch):
         rc, count, flags, recs = _noalloc(sp, torch, params, dseav, dldca, 1024, sp.SP_NOALLOC_MAX_RESULTS)
         assert rc == sp.SP_OK and flags == 0 and count == n, kw
         _same(recs, want)
+
+
+def test_noalloc_sort_beyond_one_block(sp, torch):
+    """About 20,000 results: the sort merges runs of 8,192 keys across the
+    grid, using the caller's output records as its second buffer (nothing
+    allocated); the list equals the context's, bit for bit."""
+    rng = np.random.default_rng(53)
+    hosts = rng.permutation(np.unique(rng.integers(0, 2**32, 26000, dtype=np.uint32))[:20000])
+    pairs = np.stack([np.repeat(hosts, 64), rng.integers(0, 2**32, hosts.size * 64, dtype=np.uint32)], 1)
+    params = sp.make_params(r=16, isb=(0, 8), ibn=(9, 9), theta=32, seed=53)
+    with sp.SuperPoint(params) as ctx:
+        ctx.update(torch.from_numpy(np.ascontiguousarray(pairs).reshape(-1).view(np.int32).copy()).cuda())
+        want, n, rc = ctx.detect()
+        assert rc == sp.SP_OK and n > 8192
+        seav, ldca = ctx.sketch_image()
+    dseav = torch.from_numpy(seav).cuda()
+    dldca = torch.from_numpy(ldca.view(np.int32)).cuda()
+    for _ in range(2):
+        rc, count, flags, recs = _noalloc(sp, torch, params, dseav, dldca, 0, sp.SP_NOALLOC_MAX_RESULTS)
+        assert rc == sp.SP_OK and flags == 0 and count == n
+        _same(recs, want)
