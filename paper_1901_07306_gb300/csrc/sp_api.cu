@@ -747,26 +747,37 @@ int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
     if (n_pairs[b] && (!dev_pairs[b] || ((uintptr_t)dev_pairs[b] & 7u))) return SP_ERR_PARAM;
   }
   if (capturing(ctx->stream)) return SP_ERR_STATE;
-  std::vector<uint64_t> total(ctx->p.n_routers, 0);
-  for (uint32_t b = 0; b < n_batches; ++b) total[routers[b]] += n_pairs[b];
-  for (uint32_t r = 0; r < ctx->p.n_routers; ++r)
+  const uint32_t R = ctx->p.n_routers;
+  std::vector<uint64_t> total(R, 0);
+  // the non-empty batches grouped by router, each group in call order (one counting pass)
+  std::vector<uint32_t> first(R + 1, 0), order;
+  for (uint32_t b = 0; b < n_batches; ++b) {
+    total[routers[b]] += n_pairs[b];
+    if (n_pairs[b]) ++first[routers[b] + 1];
+  }
+  for (uint32_t r = 0; r < R; ++r) first[r + 1] += first[r];
+  order.resize(first[R]);
+  {
+    std::vector<uint32_t> fill(first.begin(), first.end() - 1);
+    for (uint32_t b = 0; b < n_batches; ++b)
+      if (n_pairs[b]) order[fill[routers[b]]++] = b;
+  }
+  for (uint32_t r = 0; r < R; ++r)
     if (total[r]) ctx->slice_dirty[r] = true;
   const uint32_t bins = 1u << ctx->p.k_log2;
   std::vector<sp_batch> rest;
   rest.reserve(n_batches);
-  for (uint32_t r = 0; r < ctx->p.n_routers; ++r) {
+  for (uint32_t r = 0; r < R; ++r) {
     if (total[r] == 0) continue;
     if (!use_binned(ctx, total[r])) {
-      for (uint32_t b = 0; b < n_batches; ++b)
-        if (routers[b] == r && n_pairs[b]) rest.push_back(sp_batch{dev_pairs[b], n_pairs[b], r, 0u});
+      for (uint32_t q = first[r]; q < first[r + 1]; ++q)
+        rest.push_back(sp_batch{dev_pairs[order[q]], n_pairs[order[q]], r, 0u});
       continue;
     }
     int rc = ensure_binned(ctx, r);
     if (rc != SP_OK) return rc;
     // rounds of consecutive batches of router r, at most max_pairs each
-    std::vector<uint32_t> mine;
-    for (uint32_t b = 0; b < n_batches; ++b)
-      if (routers[b] == r && n_pairs[b]) mine.push_back(b);
+    const std::vector<uint32_t> mine(order.begin() + first[r], order.begin() + first[r + 1]);
     size_t i = 0;
     while (i < mine.size()) {
       if (n_pairs[mine[i]] > ctx->bs.max_pairs) {          // a batch that is a round by itself
@@ -967,34 +978,31 @@ int sp_autotune_binned(sp_ctx* ctx, const uint32_t* dev_pairs, uint64_t n_pairs,
 int sp_merge(sp_ctx* ctx, const uint32_t* routers, uint32_t n, uint32_t dst_router) {
   if (!ctx || (n && !routers)) return SP_ERR_PARAM;
   if (dst_router >= ctx->p.n_routers) return SP_ERR_ROUTER;
-  const uint8_t* srcs[4096];
-  uint32_t m = 0;
   for (uint32_t i = 0; i < n; ++i)
     if (routers[i] >= ctx->p.n_routers) return SP_ERR_ROUTER;
+  std::vector<const uint8_t*> srcs;                // every listed router but dst (x | x = x)
+  srcs.reserve(n);
   if (ctx->sliding) {
-    const uint8_t* ssrc[4096];
-    uint32_t ms = 0;
     for (uint32_t i = 0; i < n; ++i)
       if (ctx->slice[routers[i]] != ctx->slice[dst_router]) return SP_ERR_STATE;   // one slice clock
     int rc = commit(ctx, dst_router);
     for (uint32_t i = 0; i < n && rc == SP_OK; ++i) {
       rc = commit(ctx, routers[i]);
-      if (routers[i] != dst_router && ms < 4096) ssrc[ms++] = ctx->st_seav(routers[i]);
+      if (routers[i] != dst_router) srcs.push_back(ctx->st_seav(routers[i]));
     }
     if (rc != SP_OK) return rc;
-    return sp::launch_merge_stamp(ctx->st_seav(dst_router), ssrc, ms, ctx->st_stride, ctx->dev_clock(dst_router),
-                                  ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+    return sp::launch_merge_stamp(ctx->st_seav(dst_router), srcs.data(), (uint32_t)srcs.size(), ctx->st_stride,
+                                  ctx->dev_clock(dst_router), ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
   }
   int rc = fold_router(ctx, dst_router);
   if (rc != SP_OK) return rc;
   for (uint32_t i = 0; i < n; ++i) {
     rc = fold_router(ctx, routers[i]);
     if (rc != SP_OK) return rc;
-    if (routers[i] == dst_router) continue;   // x | x = x
-    if (m < 4096) srcs[m++] = ctx->seav(routers[i]);
+    if (routers[i] != dst_router) srcs.push_back(ctx->seav(routers[i]));
   }
-  return sp::launch_merge(ctx->seav(dst_router), srcs, m, ctx->stride, ctx->stream) == cudaSuccess
-             ? SP_OK : SP_ERR_CUDA;
+  return sp::launch_merge(ctx->seav(dst_router), srcs.data(), (uint32_t)srcs.size(), ctx->stride, ctx->stream) ==
+                 cudaSuccess ? SP_OK : SP_ERR_CUDA;
 }
 
 int sp_copy_sketch(sp_ctx* ctx, uint32_t router, void* dev_dst, uint64_t cap, uint64_t* n) {
