@@ -253,3 +253,24 @@ def test_per_slice_cuda_graph_replay(sp, torch):
             write_table(t)
             g.replay()
             check(ctx, t)
+
+
+def test_reset_range_in_a_sliding_context(sp, torch):
+    """sp_reset_range on sliding routers forgets their slices and clocks
+    (per router), leaving the others' windows intact."""
+    kw = dict(TINY, theta=16, seed=81, window_slices=3, n_routers=3)
+    op = oparams(kw)
+    a = W.uniform_pairs(5000, seed=81, n_hosts=300)
+    b = W.uniform_pairs(5000, seed=82, n_hosts=300)
+    with sp.SuperPoint(**kw) as ctx:
+        for r in range(3):
+            ctx.update(dev(torch, a), router=r)
+            ctx.slide(r)
+            ctx.update(dev(torch, b), router=r)
+        sp.sp_reset_range(ctx.ctx, 1, 2)
+        assert same_sketch(ctx, O.Sketch(op).update(a).update(b), router=0)
+        for r in (1, 2):
+            seav, ldca = ctx.sketch_image(r)
+            assert not seav.any() and not ldca.any(), r
+        ctx.update(dev(torch, b), router=1)                     # slice 0 of a fresh window
+        assert same_sketch(ctx, O.Sketch(op).update(b), router=1)
