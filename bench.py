@@ -110,6 +110,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.file = None
+        self.n0 = 0
 
     def start(self):
         try:
@@ -117,13 +118,27 @@ class ClockSampler:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
                  "-lms", "50"], stdout=self.file, stderr=subprocess.DEVNULL)
-            time.sleep(0.3)
+            # nvidia-smi's start-up (NVML initialisation) disturbs the GPU's
+            # host transfers for ~0.1 s: the timed region starts only once it
+            # has written two samples (at most 5 s)
+            self._wait_rows(2, 5.0)
+            self.n0 = self._rows()
         except Exception:
             self.proc = None
+
+    def _rows(self) -> int:
+        with open(self.file.name) as f:
+            return sum(1 for ln in f if ln.strip())
+
+    def _wait_rows(self, n: int, limit_s: float):
+        deadline = time.perf_counter() + limit_s
+        while time.perf_counter() < deadline and self.proc.poll() is None and self._rows() < n:
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self._wait_rows(self.n0 + 2, 1.0)              # samples from the timed region and just after it
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -132,6 +147,7 @@ class ClockSampler:
         self.file.flush()
         rows = [ln.strip().split(", ") for ln in open(self.file.name) if ln.strip()]
         os.unlink(self.file.name)
+        rows = rows[self.n0:] or rows                  # the start-up samples precede the timed region
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
@@ -735,11 +751,17 @@ def serving_leg(torch, sp, W, requests=400, runs=3, warmup=1, window_slices=1):
     arrivals; continuous batching under a 2 GiB staging budget vs the plain
     one-launch-per-batch path, a detect every 2^24 global pairs.  Throughput
     with the offered load above capacity (median of the runs), then
-    batch-to-result latency at half the plain path's capacity."""
+    batch-to-result latency at half the plain path's capacity (the median
+    run of each path by ack p50)."""
     from paper_1901_07306_gb300 import serving as S
     n_routers = 64
     reqs = S.poisson_requests(5, n_routers, requests, rate_pairs_per_s=1e13, lo_log2=12, hi_log2=22)
     total = sum(r.n_pairs for r in reqs)
+
+    # one server per path, made once and reused by every run (a server is
+    # long-lived: its context, arenas and pinned buffers outlast the runs)
+    servers = {b: S.SketchServer(n_routers, dict(PROFILE_S, theta=1024, seed=5), budget_bytes=2 << 30,
+                                 detect_every=1 << 24, window_slices=window_slices, batched=b) for b in (True, False)}
 
     def serve(batched, rate):
         mean = total / len(reqs)
@@ -747,28 +769,36 @@ def serving_leg(torch, sp, W, requests=400, runs=3, warmup=1, window_slices=1):
         gaps = rng.exponential(mean / rate, len(reqs))
         arr = np.cumsum(gaps) - gaps[0]
         rs = [S.Request(router=r.router, pairs=r.pairs, arrival=float(a)) for r, a in zip(reqs, arr)]
-        srv = S.SketchServer(n_routers, dict(PROFILE_S, theta=1024, seed=5), budget_bytes=2 << 30,
-                             detect_every=1 << 24, window_slices=window_slices, batched=batched)
-        try:
-            wins = srv.run(rs)
-        finally:
-            srv.close()
+        srv = servers[batched]
+        wins = srv.run(rs)
         return rs, wins, srv.elapsed
 
-    for _ in range(max(1, warmup)):                                   # warm up (allocations, build)
+    try:
+        return _serving_runs(S, serve, reqs, total, n_routers, runs, warmup, window_slices)
+    finally:
+        for srv in servers.values():
+            srv.close()
+
+
+def _serving_runs(S, serve, reqs, total, n_routers, runs, warmup, window_slices):
+    for _ in range(max(1, warmup)):                                   # warm up: first DMA of the pinned batches
         serve(True, 1e13)
+        serve(False, 1e13)
     clocks = ClockSampler(_gpu_index())
     clocks.start()
     # offered load above capacity; host-driven, so the median of several runs
     bat = sorted((serve(True, 1e13) for _ in range(runs)), key=lambda x: x[2])
     pla = sorted((serve(False, 1e13) for _ in range(runs)), key=lambda x: x[2])
-    clk = clocks.stop()
     rb, wb, tb = bat[runs // 2]
     rp, wp, tp = pla[runs // 2]
     assert all(a.n_found == b.n_found and np.array_equal(a.records, b.records) for a, b in zip(wb, wp))
     rate = 0.5 * total / tp                                          # half the plain path's capacity
-    lb, _, _ = serve(True, rate)
-    lp, _, _ = serve(False, rate)
+    lat = {"batched": [], "plain": []}
+    for _ in range(runs):                                            # alternating; the median run by ack p50
+        lat["batched"].append(S.latency_summary(serve(True, rate)[0]))
+        lat["plain"].append(S.latency_summary(serve(False, rate)[0]))
+    clk = clocks.stop()
+    med = {k: sorted(v, key=lambda x: x["ack_ms"]["p50"])[len(v) // 2] for k, v in lat.items()}
     return {"workload": f"serving: {n_routers} routers, {len(reqs)} batches of 2^12-2^22 pairs (log-uniform), Poisson "
                         "arrivals, 2 GiB staging budget, detect every 2^24 global pairs (OR-merge into a global "
                         "router), profile S (r=12, LC=2^14), "
@@ -779,8 +809,9 @@ def serving_leg(torch, sp, W, requests=400, runs=3, warmup=1, window_slices=1):
             "batched": {"value": total / tb, "unit": UNIT, "ms": tb * 1e3},
             "plain_per_batch": {"value": total / tp, "unit": UNIT, "ms": tp * 1e3},
             "batched_speedup": tp / tb,
-            "latency_at_half_plain_capacity": {"offered_pairs_per_s": rate, "batched": S.latency_summary(lb),
-                                               "plain": S.latency_summary(lp)},
+            "latency_at_half_plain_capacity": {
+                "offered_pairs_per_s": rate, "runs": runs, "batched": med["batched"], "plain": med["plain"],
+                "runs_ack_p50_ms": {k: [round(x["ack_ms"]["p50"], 3) for x in v] for k, v in lat.items()}},
             "clocks": clk}
 
 

@@ -196,6 +196,18 @@ SP_API int sp_set_stream(sp_ctx* ctx, void* cuda_stream);
  * SP_ERR_PARAM (ctx NULL). */
 SP_API int sp_set_timeout(sp_ctx* ctx, uint32_t timeout_ms);
 
+/* Allocates now the device and pinned host buffers that updates of routers
+ * first .. first + count - 1 would otherwise allocate on first use: the two
+ * staging buffers of sp_update_host, the ring of batch tables of
+ * sp_update_batched (room for 1,024 batches per call each), and, where the
+ * binned scan applies to the parameter set, its bin lists and the routers'
+ * accumulator planes.  A loop that must not stall on an allocation (a server
+ * acknowledging batches) calls it once before it starts.  Optional: every
+ * update still allocates what is missing.  Synchronous on the host (it
+ * allocates), issues no stream work.  Errors: SP_ERR_PARAM (ctx NULL),
+ * SP_ERR_ROUTER (range outside the context), SP_ERR_NOMEM, SP_ERR_CUDA. */
+SP_API int sp_reserve(sp_ctx* ctx, uint32_t first, uint32_t count);
+
 /* Copy of the parameters the context was created with. */
 SP_API int sp_get_params(const sp_ctx* ctx, sp_params* out);
 

@@ -697,23 +697,39 @@ static bool capturing(cudaStream_t st) {
 
 // Uploads n entries of a batch table through the next pinned slot of the
 // ring; *dev receives the slot's device copy.
-static int upload_table(sp_ctx* ctx, const sp_batch* tab, uint32_t n, const sp_batch** dev) {
-  sp_ctx::TableSlot& t = ctx->tables[ctx->table_next++ % sp_ctx::kTableRing];
-  if (n > t.cap) {
-    const int wrc = wait_stream(ctx);                                        // old copy no longer read
+// Gives a table slot room for n batches.  A slot that was never allocated
+// costs no wait; growing a used one waits for the stream first, since a
+// launch issued after its last upload may still read the old device copy.
+static int grow_table_slot(sp_ctx* ctx, sp_ctx::TableSlot& t, uint32_t n) {
+  if (n <= t.cap) return SP_OK;
+  if (t.host) {
+    const int wrc = wait_stream(ctx);
     if (wrc != SP_OK) return wrc;
-    if (t.host) cudaFreeHost(t.host);
+    cudaFreeHost(t.host);
     cudaFree(t.dev);
     t.host = nullptr;
     t.dev = nullptr;
     t.cap = 0;
     t.pending = false;
-    const uint32_t cap = n < 1024 ? 1024 : n;
-    if (cudaMallocHost(&t.host, cap * sizeof(sp_batch)) != cudaSuccess ||
-        cudaMalloc(&t.dev, cap * sizeof(sp_batch)) != cudaSuccess) { cudaGetLastError(); return SP_ERR_NOMEM; }
-    t.cap = cap;
   }
+  const uint32_t cap = n < 1024 ? 1024 : n;
+  if (cudaMallocHost(&t.host, cap * sizeof(sp_batch)) != cudaSuccess ||
+      cudaMalloc(&t.dev, cap * sizeof(sp_batch)) != cudaSuccess) {
+    cudaGetLastError();
+    if (t.host) cudaFreeHost(t.host);
+    t.host = nullptr;
+    t.dev = nullptr;
+    return SP_ERR_NOMEM;
+  }
+  t.cap = cap;
   if (!t.ev && cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming) != cudaSuccess) return SP_ERR_CUDA;
+  return SP_OK;
+}
+
+static int upload_table(sp_ctx* ctx, const sp_batch* tab, uint32_t n, const sp_batch** dev) {
+  sp_ctx::TableSlot& t = ctx->tables[ctx->table_next++ % sp_ctx::kTableRing];
+  const int grc = grow_table_slot(ctx, t, n);
+  if (grc != SP_OK) return grc;
   if (t.pending) {
     const int wrc = wait_event_bounded(ctx, t.ev);
     if (wrc != SP_OK) return wrc;
@@ -735,6 +751,16 @@ static int launch_table(sp_ctx* ctx, const sp_batch* dev_tab, uint32_t n) {
       return SP_ERR_CUDA;
   }
   return SP_OK;
+}
+
+int sp_reserve(sp_ctx* ctx, uint32_t first, uint32_t count) {
+  if (!ctx) return SP_ERR_PARAM;
+  if (first > ctx->p.n_routers || count > ctx->p.n_routers - first) return SP_ERR_ROUTER;
+  int rc = ensure_staging(ctx);
+  for (int i = 0; rc == SP_OK && i < sp_ctx::kTableRing; ++i) rc = grow_table_slot(ctx, ctx->tables[i], 1);
+  if (rc != SP_OK || !sp::binned_applicable(ctx->d)) return rc;
+  for (uint32_t r = first; rc == SP_OK && r < first + count; ++r) rc = ensure_binned(ctx, r);
+  return rc;
 }
 
 int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,

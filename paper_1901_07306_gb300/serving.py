@@ -119,9 +119,19 @@ class GpuOps:
         self.window_slices = window_slices
         self.batched = batched
         self.report_cap = report_cap
+        # nothing in the serving loop allocates: the library's lazy buffers
+        # (staging, batch tables, bin lists, planes) and a few pinned result
+        # buffers are made here (a pinned or device allocation can stall the
+        # host for milliseconds)
+        sp.sp_reserve(self.ctx.ctx, 0, n_routers)
+        self.result_bufs = [self._result_buf() for _ in range(4)]
 
     def close(self):
         self.ctx.close()
+
+    def _result_buf(self):
+        out_t = torch.empty(self.report_cap * self.sp.CANDIDATE.itemsize, dtype=torch.uint8).pin_memory()
+        return out_t, torch.zeros(2, dtype=torch.int32).pin_memory()
 
     def synchronize(self):
         torch.cuda.synchronize()
@@ -164,9 +174,7 @@ class GpuOps:
         with torch.cuda.stream(self.compute):
             sp.sp_merge(c, list(range(self.n_routers)), self.gs)
             sp.sp_detect_async(c, self.gs, 0)
-            out = np.zeros(self.report_cap, sp.CANDIDATE)
-            out_t = torch.from_numpy(out.view(np.uint8)).pin_memory()
-            status = torch.zeros(2, dtype=torch.int32).pin_memory()
+            out_t, status = self.result_bufs.pop() if self.result_bufs else self._result_buf()
             sp.sp_results_async(c, out_t, self.report_cap, status)
             if self.window_slices > 1:
                 for r in range(self.n_routers + 1):
@@ -181,7 +189,9 @@ class GpuOps:
         """(super points found, their records) of a completed detection."""
         out_t, status = handle
         cnt, _flags = (int(x) for x in status.numpy().view(np.uint32))
-        return cnt, out_t.numpy().view(self.sp.CANDIDATE)[:min(cnt, self.report_cap)].copy()
+        recs = out_t.numpy().view(self.sp.CANDIDATE)[:min(cnt, self.report_cap)].copy()
+        self.result_bufs.append(handle)                       # free for a later window
+        return cnt, recs
 
 
 class SketchServer:
@@ -213,12 +223,15 @@ class SketchServer:
         self.ops.close()
 
     def run(self, requests: list[Request]):
-        """Serves the requests (sorted by arrival); returns self.windows.
+        """Serves the requests (sorted by arrival); returns self.windows, the
+        windows of this call (a server may run several request lists in turn:
+        every call ends with its last window closed and the routers reset).
         Raises ServingTimeout when a step's scan or a window's detection has
         not completed timeout_s after it was issued.  Python's cyclic garbage
         collector is paused while the loop runs (a collection can stall the
         host for tens of milliseconds, a latency spike for every request in
         flight)."""
+        self.windows = []
         was_enabled = gc.isenabled()
         gc.disable()
         try:

@@ -43,7 +43,7 @@ EXPORTED = (
     "sp_export", "sp_import", "sp_detect_noalloc", "sp_update_batched_device", "sp_autotune",
     "sp_results_async", "sp_psu", "sp_size_ldca", "sp_set_timeout", "sp_copy_sketch", "sp_merge_device",
     "sp_binned_shapes", "sp_set_binned_shape", "sp_get_binned_shape", "sp_autotune_binned",
-    "sp_reset_range", "sp_update_batched_host",
+    "sp_reset_range", "sp_update_batched_host", "sp_reserve",
 )
 
 
@@ -105,6 +105,7 @@ def _load():
         "sp_destroy": (None, [vp]),
         "sp_set_stream": (i32, [vp, vp]),
         "sp_set_timeout": (i32, [vp, u32]),
+        "sp_reserve": (i32, [vp, u32, u32]),
         "sp_get_params": (i32, [vp, P(sp_params)]),
         "sp_reset": (i32, [vp, u32]),
         "sp_reset_range": (i32, [vp, u32, u32]),
@@ -229,6 +230,14 @@ def sp_set_stream(ctx: int, stream) -> None:
 
 def sp_set_timeout(ctx: int, timeout_ms: int) -> None:
     _check(lib.sp_set_timeout(ctypes.c_void_p(ctx), timeout_ms), "sp_set_timeout")
+
+
+def sp_reserve(ctx: int, first: int = 0, count: int | None = None) -> None:
+    """Allocates up front what updates of routers first .. first + count - 1
+    would allocate on first use (default: every router)."""
+    if count is None:
+        count = sp_get_params(ctx).n_routers - first
+    _check(lib.sp_reserve(ctypes.c_void_p(ctx), first, count), "sp_reserve")
 
 
 def sp_get_params(ctx: int) -> sp_params:

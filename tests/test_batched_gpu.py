@@ -242,3 +242,29 @@ def test_batched_host_copies_into_arena(sp, torch):
         for r in range(3):
             mine = [x for rr, x in zip(routers, data) if rr == r]
             assert same_sketch(ctx, O.Sketch(oparams(kw)).update(np.concatenate(mine)), r), r
+
+
+def test_reserve_then_batched_and_host_updates(sp, torch):
+    """sp_reserve allocates up front what updates would allocate on first use;
+    afterwards the batched scan (binned and direct routers, then a call with
+    more batches than a reserved table holds, which grows a used table) and
+    the host path give the oracle's sketches.  A range outside the context is
+    refused."""
+    kw = dict(theta=256, seed=19, n_routers=4)
+    big = [W.uniform_pairs(n, seed=190 + i, n_hosts=50000) for i, n in enumerate((1 << 21, (1 << 21) + 7))]
+    small = [W.uniform_pairs(64 + 3 * i, seed=200 + i, n_hosts=40) for i in range(1500)]
+    with sp.SuperPoint(**kw) as ctx:
+        with pytest.raises(sp.SPError) as e:
+            sp.sp_reserve(ctx.ctx, 2, 3)
+        assert e.value.code == sp.SP_ERR_ROUTER
+        sp.sp_reserve(ctx.ctx, 0, 0)                       # no router: only the shared buffers
+        sp.sp_reserve(ctx.ctx)
+        sp.sp_reserve(ctx.ctx)                             # idempotent
+        sp.sp_update_batched(ctx.ctx, [1, 0, 1], [dev(torch, big[0]), dev(torch, small[0]), dev(torch, big[1])])
+        sp.sp_update_batched(ctx.ctx, [2] * len(small), [dev(torch, x) for x in small])
+        host = torch.from_numpy(np.ascontiguousarray(big[0], np.uint32).reshape(-1).view(np.int32).copy()).pin_memory()
+        sp.sp_update_host(ctx.ctx, 3, host)
+        op = oparams(kw)
+        want = {0: small[0], 1: np.concatenate(big), 2: np.concatenate(small), 3: big[0]}
+        for r, pairs in want.items():
+            assert same_sketch(ctx, O.Sketch(op).update(pairs), r), r

@@ -443,3 +443,44 @@ def test_reset_range(sp, torch):
         with pytest.raises(sp.SPError) as e:
             sp.sp_reset_range(ctx.ctx, 3, 2)
         assert e.value.code == sp.SP_ERR_ROUTER
+
+
+def _random_profile(rng):
+    """A random parameter set inside the library's limits that satisfies the
+    coverage and overlap constraints of Sec. 3.2 (checked by the oracle)."""
+    while True:
+        r = int(rng.integers(4, 20))
+        L = 32 - r
+        sr = int(rng.integers(2, 6))
+        step = -(-L // sr)
+        ibn = [int(min(12, L, step + rng.integers(1, 4))) for _ in range(sr)]
+        isb = [(i * step + int(rng.integers(0, 2))) % L for i in range(sr)]
+        k_log2 = int(rng.integers(5, 12))
+        lr = int(rng.integers(1, 9))
+        lc_log2 = int(rng.integers(5, 15))
+        if (lr << lc_log2) > (1 << 20) or sum(1 << b for b in ibn) > 4096:
+            continue
+        kw = dict(r=r, isb=tuple(isb), ibn=tuple(ibn), k_log2=k_log2, lr=lr, lc_log2=lc_log2)
+        if O.check_params(oracle_params(dict(kw, theta=64, seed=1))) == 0:
+            return kw
+
+
+@pytest.mark.parametrize("case", range(12))
+def test_random_profiles_both_scan_forms(sp, torch, case):
+    """Seeded random profiles: every scan form gives the oracle's sketch and
+    detection bit for bit (one-word LDCs, 32-bit LDCA rows, up to 8 rows,
+    k up to 2048 -- the binned form applies up to k = 1024)."""
+    rng = np.random.default_rng(700 + case)
+    kw = dict(_random_profile(rng), theta=int(rng.choice([48, 64, 256])), seed=700 + case)
+    pairs, _ = W.single_window(seed=710 + case, n=int(rng.integers(1 << 14, 1 << 17)), n_background=2048,
+                               n_planted=4, planted_degree=400)
+    osk = O.Sketch(oracle_params(kw)).update(pairs)
+    want, n_want, overflow = osk.detect()
+    for mode in (1, 2):
+        with sp.SuperPoint(**dict(kw, scan_mode=mode)) as ctx:
+            ctx.update(dev(torch, pairs, case % 2))
+            assert_same_sketch(ctx, osk)
+            got, n, rc = ctx.detect()
+            if not overflow:
+                assert n == n_want and rc in (sp.SP_OK, sp.SP_ERR_TRUNCATED)
+                assert_same_results(got, want[:len(got)])
