@@ -748,7 +748,8 @@ def sliding_leg(torch, sp, W, total_log2=28, passes=2, warmup=1, checkpoints=())
 
 def serving_leg(torch, sp, W, requests=400, runs=3, warmup=1, window_slices=1):
     """64 routers sending batches of 2^12-2^22 pairs (log-uniform) with Poisson
-    arrivals; continuous batching under a 2 GiB staging budget vs the plain
+    arrivals; continuous batching (each step's pinned batches scanned in place
+    by one batched call) under a 2 GiB in-flight budget vs the plain
     one-launch-per-batch path, a detect every 2^24 global pairs.  Throughput
     with the offered load above capacity (median of the runs), then
     batch-to-result latency at half the plain path's capacity (the median
@@ -759,7 +760,7 @@ def serving_leg(torch, sp, W, requests=400, runs=3, warmup=1, window_slices=1):
     total = sum(r.n_pairs for r in reqs)
 
     # one server per path, made once and reused by every run (a server is
-    # long-lived: its context, arenas and pinned buffers outlast the runs)
+    # long-lived: its context and pinned result buffers outlast the runs)
     servers = {b: S.SketchServer(n_routers, dict(PROFILE_S, theta=1024, seed=5), budget_bytes=2 << 30,
                                  detect_every=1 << 24, window_slices=window_slices, batched=b) for b in (True, False)}
 
@@ -800,7 +801,8 @@ def _serving_runs(S, serve, reqs, total, n_routers, runs, warmup, window_slices)
     clk = clocks.stop()
     med = {k: sorted(v, key=lambda x: x["ack_ms"]["p50"])[len(v) // 2] for k, v in lat.items()}
     return {"workload": f"serving: {n_routers} routers, {len(reqs)} batches of 2^12-2^22 pairs (log-uniform), Poisson "
-                        "arrivals, 2 GiB staging budget, detect every 2^24 global pairs (OR-merge into a global "
+                        "arrivals, batched steps read the pinned batches in place, 2 GiB in-flight budget, detect every "
+                        "2^24 global pairs (OR-merge into a global "
                         "router), profile S (r=12, LC=2^14), "
                         + (f"sliding window of {window_slices} detect periods" if window_slices > 1
                            else "discrete windows") + "; value = median of the runs (host wall clock)",

@@ -256,9 +256,13 @@ typedef struct sp_batch {
  * at least 2^22 pairs take the binned scan (one binning launch per batch, one
  * plane launch per router); all other batches are scanned by ONE persistent
  * launch over a batch table, whose block shape comes from sp_autotune (or a
- * default).  Same per-batch semantics and errors as sp_update.  Async; the
- * table goes to the device through a context-owned pinned buffer, so the call
- * is not valid inside a stream capture (SP_ERR_STATE): capture
+ * default).  Same per-batch semantics and errors as sp_update.  A stream may
+ * also be page-locked host memory mapped into the device's address space
+ * (cudaHostAlloc or cudaHostRegister; under unified addressing the host
+ * pointer is the device pointer): the kernels then read it in place across
+ * the host link (NVLink-C2C on a Grace-Blackwell node), with no staging copy.
+ * Async; the table goes to the device through a context-owned pinned buffer,
+ * so the call is not valid inside a stream capture (SP_ERR_STATE): capture
  * sp_update_batched_device instead. */
 SP_API int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
                              const uint32_t* const* dev_pairs, const uint64_t* n_pairs);

@@ -7,12 +7,16 @@ in the library's kernels; this module only schedules.
 
 Engine (``SketchServer.run``):
   * admission -- requests are admitted in arrival order while their bytes fit
-    a fixed device staging budget (``budget_bytes``); a request that does not
-    fit waits until earlier ones have been scanned and freed their room.
-  * continuous batching -- every engine step copies the newly admitted
-    requests host-to-device on a copy stream (pinned host memory), then scans
-    all of them with ONE ``sp_update_batched`` call on the compute stream;
-    while the GPU works on step s the host admits and copies step s + 1.
+    a fixed budget of pinned host memory in flight (``budget_bytes``: bytes
+    admitted and not yet scanned); a request that does not fit waits until
+    earlier ones have been scanned and freed their room.
+  * continuous batching -- every engine step scans all newly admitted
+    requests with ONE ``sp_update_batched`` call on the compute stream.  The
+    kernels read each request's pinned host pairs in place, across the host
+    link (NVLink-C2C to the Grace CPU on a GB300; pinned memory is mapped into
+    the device's address space), so a step has no staging copy, no copy
+    stream and no device arena, and its scan streams its input once.  While
+    the GPU works on step s the host admits and issues step s + 1.
   * windows -- every ``detect_every`` admitted pairs close a window (a time
     slice): the routers are OR-merged into the global router, it is detected
     asynchronously, and the routers start the next window (reset, or slide
@@ -24,7 +28,7 @@ Engine (``SketchServer.run``):
     ``ServingTimeout`` (the paper has no such step; a watch point whose GPU
     stopped making progress is reported instead of waited on forever).
 
-The device side sits behind ``GpuOps`` (context, streams, staging arenas),
+The device side sits behind ``GpuOps`` (context, stream, result buffers),
 so the scheduling, admission and deadline logic of ``SketchServer`` can also
 be driven by a stand-in with the same methods.
 
@@ -76,8 +80,8 @@ class ServingTimeout(TimeoutError):
 
 
 class _Budget:
-    """Admission by a fixed device-memory budget: bytes of admitted requests
-    whose scan has not completed yet."""
+    """Admission by a fixed budget: bytes of admitted requests whose scan has
+    not completed yet (their pinned host memory is still read by the GPU)."""
 
     def __init__(self, budget_bytes: int):
         self.budget = int(budget_bytes)
@@ -97,13 +101,12 @@ class _Budget:
 
 class GpuOps:
     """The server's device side: one library context holding routers
-    0 .. n_routers - 1 plus the global router n_routers, a compute and a copy
-    stream, and (batched engine) two staging arenas of half the budget each:
-    step s fills arena s % 2 and may reuse it once the scan of step s - 2 has
-    completed."""
+    0 .. n_routers - 1 plus the global router n_routers, on one compute
+    stream.  The batched engine scans a step's requests where they lie
+    (pinned host or device memory); the plain path copies each request
+    through the library's staging buffers (sp_update_host)."""
 
-    def __init__(self, n_routers: int, params: dict | None, budget_bytes: int, window_slices: int,
-                 batched: bool, report_cap: int):
+    def __init__(self, n_routers: int, params: dict | None, window_slices: int, batched: bool, report_cap: int):
         from . import sp
         self.sp = sp
         self.n_routers = n_routers
@@ -111,11 +114,7 @@ class GpuOps:
         kw = dict(params or {})
         kw.update(n_routers=n_routers + 1, window_slices=window_slices)
         self.compute = torch.cuda.Stream()
-        self.copy = torch.cuda.Stream()
         self.ctx = sp.SuperPoint(sp.make_params(**kw), stream=self.compute)
-        half = (int(budget_bytes) // 2) // 8 * 2             # int32 words, whole pairs
-        self.arenas = [torch.empty(half, dtype=torch.int32, device="cuda") for _ in range(2)] if batched else []
-        self.arena_free = [None, None]                        # event of the last step that read the arena
         self.window_slices = window_slices
         self.batched = batched
         self.report_cap = report_cap
@@ -136,34 +135,24 @@ class GpuOps:
     def synchronize(self):
         torch.cuda.synchronize()
 
-    def arena_words(self) -> int:
-        """int32 words of one staging arena (0: the plain path stages nothing)."""
-        return self.arenas[0].numel() if self.batched else 0
-
-    def arena_ready(self, arena: int) -> bool:
-        return not self.batched or self.arena_free[arena] is None or self.arena_free[arena].query()
-
-    def issue_step(self, step: list, arena: int, offsets: list):
-        """Copies the step's requests into the arena and scans them with one
-        batched call (batched engine: sp_update_batched_host, which packs the
-        requests at the word offsets the engine computed -- 16-byte
-        boundaries -- and runs the copy loop in C), or copies and scans each
-        on its own (plain path).  Returns the event that completes with the
-        step's scan."""
+    def issue_step(self, step: list):
+        """Scans the step's requests: one batched call that reads every
+        request in place (batched engine), or one copy + one launch per
+        request (plain path).  Returns the event that completes with the
+        step's scan; the requests' memory must stay valid until then."""
         sp, c = self.sp, self.ctx.ctx
-        if self.batched:
-            if self.arena_free[arena] is not None:
-                self.copy.wait_event(self.arena_free[arena])      # the last scan that read this arena
-            sp.sp_update_batched_host(c, [r.router for r in step], [r.pairs for r in step], self.arenas[arena],
-                                      self.copy)
-        else:
-            with torch.cuda.stream(self.compute):
-                for r in step:                                # one copy + one launch each
+        with torch.cuda.stream(self.compute):
+            if self.batched:
+                for r in step:
+                    if not (r.pairs.is_cuda or r.pairs.is_pinned()):
+                        raise ValueError("the batched engine reads requests in place: give pinned host tensors "
+                                         "(Tensor.pin_memory) or CUDA tensors")
+                sp.sp_update_batched(c, [r.router for r in step], [r.pairs for r in step])
+            else:
+                for r in step:
                     sp.sp_update_host(c, r.router, r.pairs)
         ev = torch.cuda.Event()
         ev.record(self.compute)
-        if self.batched:
-            self.arena_free[arena] = ev
         return ev
 
     def close_window(self):
@@ -214,8 +203,7 @@ class SketchServer:
         self.max_step = max_step_requests
         self.batched = batched
         self.timeout_s = float(timeout_s)
-        self.ops = ops if ops is not None else GpuOps(n_routers, params, budget_bytes, window_slices, batched,
-                                                      report_cap)
+        self.ops = ops if ops is not None else GpuOps(n_routers, params, window_slices, batched, report_cap)
         self.windows: list[WindowResult] = []
         self.elapsed = float("nan")
 
@@ -247,7 +235,6 @@ class SketchServer:
         detects = deque()         # (event, issued at, WindowResult, handle, requests)
         window, window_pairs, window_reqs = 0, 0, []
         n_steps = 0
-        arena_words = ops.arena_words()
         ops.synchronize()
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0  # noqa: E731
@@ -278,22 +265,11 @@ class SketchServer:
                 raise ServingTimeout(f"the detection of window {detects[0][2].index} has not completed "
                                      f"{self.timeout_s:g} s after it was issued")
             # admit what has arrived, in order, within the budget and the window
-            step, offsets = [], []
+            step = []
             boundary = False
-            arena = n_steps % 2 if self.batched else 0
-            arena_ready = ops.arena_ready(arena)
-            used = 0
-            while arena_ready and pending and pending[0].arrival <= now() and len(step) < self.max_step \
+            while pending and pending[0].arrival <= now() and len(step) < self.max_step \
                     and self.budget.fits(pending[0].nbytes):
                 r = pending[0]
-                if self.batched:
-                    words = (r.pairs.numel() + 3) // 4 * 4                # packed at 16-byte boundaries
-                    if words > arena_words:
-                        raise ValueError(f"a {r.nbytes}-byte request exceeds half the staging budget")
-                    if used + words > arena_words:
-                        break                                         # this step's arena is full
-                    offsets.append(used)
-                    used += words
                 pending.popleft()
                 self.budget.take(r.nbytes)                            # charged as it is admitted
                 r.window = window
@@ -306,7 +282,7 @@ class SketchServer:
             if not pending and window_reqs and not step and not boundary:
                 boundary = True                                       # the last, partial window
             if step:
-                ev = ops.issue_step(step, arena, offsets)
+                ev = ops.issue_step(step)
                 steps.append((ev, now(), step, sum(r.nbytes for r in step), n_steps))
                 n_steps += 1
                 progressed = True

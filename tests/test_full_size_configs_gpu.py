@@ -180,7 +180,7 @@ def test_serving_64_routers_full_size(sp, torch):
         srv = S.SketchServer(n_routers, kw, budget_bytes=2 << 30, detect_every=1 << 24, batched=batched)
         if steps is not None:
             issue = srv.ops.issue_step
-            srv.ops.issue_step = lambda step, arena, offsets: (steps.append(step), issue(step, arena, offsets))[1]
+            srv.ops.issue_step = lambda step: (steps.append(step), issue(step))[1]
         try:
             wins = srv.run(rs)
         finally:

@@ -27,8 +27,8 @@ class FakeEvent:
 
 
 class FakeOps:
-    def __init__(self, hang_step=None, hang_window=None, words=1 << 20):
-        self.hang_step, self.hang_window, self.words = hang_step, hang_window, words
+    def __init__(self, hang_step=None, hang_window=None):
+        self.hang_step, self.hang_window = hang_step, hang_window
         self.steps, self.windows = [], []
 
     def close(self):
@@ -37,14 +37,8 @@ class FakeOps:
     def synchronize(self):
         pass
 
-    def arena_words(self):
-        return self.words
-
-    def arena_ready(self, arena):
-        return True
-
-    def issue_step(self, step, arena, offsets):
-        self.steps.append(([r.router for r in step], arena, list(offsets)))
+    def issue_step(self, step):
+        self.steps.append([id(r) for r in step])
         return FakeEvent(None if len(self.steps) - 1 == self.hang_step else 3)
 
     def close_window(self):
@@ -73,10 +67,9 @@ def test_windows_acks_and_budget_with_a_stand_in():
     assert [w.index for w in wins] == [0, 1, 2, 3] and [w.n_found for w in wins] == [100, 101, 102, 103]
     assert [r.window for r in reqs] == [i // 10 for i in range(40)]
     assert all(np.isfinite(r.t_ack) and np.isfinite(r.t_result) for r in reqs)
-    # steps hold at most 4 requests, alternate arenas, and pack them back to back
-    for k, (routers, arena, offsets) in enumerate(srv.ops.steps):
-        assert 1 <= len(routers) <= 4 and arena == k % 2
-        assert offsets == [128 * j for j in range(len(routers))]
+    # steps hold 1 to 4 requests and issue every request once, in arrival order
+    assert all(1 <= len(st) <= 4 for st in srv.ops.steps)
+    assert [x for st in srv.ops.steps for x in st] == [id(r) for r in reqs]
 
 
 @pytest.mark.parametrize("hang", ["step", "window"])
@@ -92,7 +85,7 @@ def test_a_wait_that_never_completes_raises_after_its_bound(hang):
     assert ("scan of step 2" in str(e.value)) if hang == "step" else ("detection of window 0" in str(e.value))
 
 
-def test_request_larger_than_an_arena_is_refused():
-    srv = S.SketchServer(1, budget_bytes=1 << 20, ops=FakeOps(words=100))
+def test_request_larger_than_the_budget_is_refused():
+    srv = S.SketchServer(1, budget_bytes=64 * 8 - 4, ops=FakeOps())
     with pytest.raises(ValueError):
         srv.run(_requests(1, size=64))

@@ -112,3 +112,30 @@ def test_sliding_windows(serving):
     for w in wins:
         want, n, _ = _oracle_window(reqs, {w.index - 2, w.index - 1, w.index}, op)
         assert w.n_found == n and np.array_equal(w.records["ip"], want["ip"])
+
+
+def test_batched_engine_reads_requests_in_place(serving):
+    """The batched engine scans each request where it lies: device tensors
+    give the same windows as pinned host tensors, and a pageable host tensor
+    (not guaranteed readable by the device) is refused before any launch."""
+    reqs = _requests(serving, seed=11, n=40)
+    total = sum(r.n_pairs for r in reqs)
+    kw = dict(budget_bytes=8 << 20, detect_every=total // 3 + 1)
+    srv = serving.SketchServer(8, PARAMS, **kw)
+    try:
+        host = srv.run(reqs)
+        on_dev = [serving.Request(router=r.router, pairs=r.pairs.cuda(), arrival=r.arrival) for r in reqs]
+        dev = srv.run(on_dev)
+    finally:
+        srv.close()
+    assert len(host) == len(dev) >= 3
+    for a, b in zip(host, dev):
+        assert a.n_found == b.n_found and np.array_equal(a.records, b.records)
+    pageable = [serving.Request(router=r.router, pairs=r.pairs.clone(), arrival=r.arrival) for r in reqs[:4]]
+    assert not pageable[0].pairs.is_pinned()
+    srv = serving.SketchServer(8, PARAMS, **kw)
+    try:
+        with pytest.raises(ValueError):
+            srv.run(pageable)
+    finally:
+        srv.close()
