@@ -585,6 +585,22 @@ static int commit_window(sp_ctx* ctx, uint32_t router) {
   return SP_OK;
 }
 
+// Sliding contexts, before a detect: commits the slice's SEAV bits and
+// writes the window SEAV (one pass over the SEAV stamps).  The slice's LDCA
+// bits stay in the bit sketch until the slice closes (or a merge or export
+// reads the window): the detect reads them there, beside the active stamps
+// of the lines it tests, instead of streaming the LDCA stamps.
+static int commit_seav_window(sp_ctx* ctx, uint32_t router) {
+  int rc = fold_router(ctx, router);
+  if (rc != SP_OK) return rc;
+  if (sp::launch_commit_window(reinterpret_cast<uint32_t*>(ctx->seav(router)), ctx->st_seav(router),
+                               ctx->seav_words(), ctx->ldca(router), ctx->st_ldca(router), 0,
+                               reinterpret_cast<uint32_t*>(ctx->wseav(router)), ctx->wldca(router),
+                               ctx->dev_clock(router), ctx->p.window_slices, ctx->stream) != cudaSuccess)
+    return SP_ERR_CUDA;
+  return SP_OK;
+}
+
 int sp_reset(sp_ctx* ctx, uint32_t router) {
   if (!ctx) return SP_ERR_PARAM;
   if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
@@ -1065,14 +1081,19 @@ int sp_detect_async(sp_ctx* ctx, uint32_t router, uint32_t threshold) {
   if (router >= ctx->p.n_routers) return SP_ERR_ROUTER;
   if (threshold == 0) threshold = ctx->p.theta;
   const uint32_t zt = sp_z_theta(ctx->p.k_log2, threshold);
-  int frc = ctx->sliding ? commit_window(ctx, router) : fold_router(ctx, router);
+  int frc = ctx->sliding ? commit_seav_window(ctx, router) : fold_router(ctx, router);
   if (frc != SP_OK) return frc;
   if (cudaMemsetAsync(ctx->status, 0, sizeof(DetectStatus), ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
-  // a sliding router is detected on its window image
-  const uint8_t* seav = ctx->sliding ? ctx->wseav(router) : ctx->seav(router);
-  const uint32_t* ldca = ctx->sliding ? ctx->wldca(router) : ctx->ldca(router);
-  if (sp::launch_detect(ctx->d, seav, ldca, zt, ctx->keys, ctx->cap, ctx->p.max_join, ctx->status,
-                        ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
+  // a sliding router is detected on its window SEAV and, for the LDCA test of
+  // each tested host, the active stamps and pending slice bits of its lines
+  const cudaError_t de =
+      ctx->sliding
+          ? sp::launch_detect_sliding(ctx->d, ctx->wseav(router), ctx->ldca(router), ctx->st_ldca(router),
+                                      ctx->dev_clock(router), ctx->p.window_slices, zt, ctx->keys, ctx->cap,
+                                      ctx->p.max_join, ctx->status, ctx->stream)
+          : sp::launch_detect(ctx->d, ctx->seav(router), ctx->ldca(router), zt, ctx->keys, ctx->cap,
+                              ctx->p.max_join, ctx->status, ctx->stream);
+  if (de != cudaSuccess) return SP_ERR_CUDA;
   if (sp::launch_sort_emit(ctx->keys, ctx->cap, ctx->status, ctx->est_table, ctx->p.k_log2,
                            ctx->records, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
   ctx->detect_issued = true;

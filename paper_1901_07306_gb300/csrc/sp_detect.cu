@@ -16,7 +16,9 @@
 //      the lanes (one coalesced load per row and lane), z0 = k - popc by a
 //      warp reduction.  The host survives when z0 <= Z_theta, the integer
 //      form of Est >= threshold (Eq. 4).  A full queue falls back to the
-//      same test in one lane.
+//      same test in one lane.  For a sliding router (Sec. 5.2) a line word
+//      is the union of the slice bits not yet committed and the 32 stamps of
+//      the word that are active at the router's slice clock.
 //   Survivors are appended as (ip << 32 | z0) keys with one atomic per hit.
 // k_sort_emit: sorts the keys by ip (ascending; ips are unique) and writes
 //   sp_candidate records with est taken from a table of -k ln(z0 / k).  Up to
@@ -49,28 +51,58 @@ struct Found {
   DetectStatus* status;
 };
 
-__device__ __forceinline__ uint32_t ldc_zeros(const DevParams& d, const uint32_t* __restrict__ ldca, uint32_t ip) {
+// Where the LDCA test reads the bits of an LDC line.  Discrete window: the
+// LDCA itself.  Sliding window (Sec. 5.2): word w of the window LDCA is the
+// union of the bits of the slice sketch not yet committed (bits[w]) and the
+// stamps of word w (32 bytes at stamps + 32 w) active at the router's clock.
+// Only the lines of tested hosts are read, so a detect touches a few MB of
+// stamps instead of streaming the whole counter pool.
+struct LdcaRead {
+  const uint32_t* bits;
+  const uint4* stamps;
+  uint32_t cur4, k4;
+};
+
+template <bool kSliding>
+__device__ __forceinline__ uint32_t ldc_word(const LdcaRead& a, uint64_t w) {
+  if (!kSliding) return a.bits[w];
+  return a.bits[w] | active32(a.stamps[2 * w], a.stamps[2 * w + 1], a.cur4, a.k4);
+}
+
+// word index of the first word of host ip's LDC line in LDCA row i
+__device__ __forceinline__ uint64_t ldc_line(const DevParams& d, uint32_t ip, uint32_t i) {
+  const uint32_t col = (uint32_t)((uint64_t)mas(d.ha[2 + i], d.hb[2 + i], ip) >> (32u - d.lc_log2));
+  return (uint64_t)((i << d.lc_log2) | col) << (d.k_log2 - 5u);
+}
+
+template <bool kSliding>
+__device__ __forceinline__ uint32_t ldc_zeros(const DevParams& d, const LdcaRead& a, uint32_t ip) {
   const uint32_t wpl = 1u << (d.k_log2 - 5u);
-  const uint32_t cshift = 32u - d.lc_log2;
-  const uint32_t* line[8];
-  for (uint32_t i = 0; i < d.lr; ++i) {
-    const uint32_t col = (uint32_t)((uint64_t)mas(d.ha[2 + i], d.hb[2 + i], ip) >> cshift);
-    line[i] = ldca + ((uint64_t)((i << d.lc_log2) | col) << (d.k_log2 - 5u));
-  }
+  uint64_t line[8];
+  for (uint32_t i = 0; i < d.lr; ++i) line[i] = ldc_line(d, ip, i);
   uint32_t ones = 0;
+  if (kSliding) {
+    for (uint32_t w = 0; w < wpl; ++w) {
+      uint32_t u = ldc_word<true>(a, line[0] + w);
+      for (uint32_t i = 1; i < d.lr; ++i) u &= ldc_word<true>(a, line[i] + w);
+      ones += __popc(u);
+    }
+    return (1u << d.k_log2) - ones;
+  }
+  const uint32_t* ldca = a.bits;
   if (wpl >= 4) {
     for (uint32_t w = 0; w < wpl; w += 4) {
-      uint4 u = *reinterpret_cast<const uint4*>(line[0] + w);
+      uint4 u = *reinterpret_cast<const uint4*>(ldca + line[0] + w);
       for (uint32_t i = 1; i < d.lr; ++i) {
-        const uint4 v = *reinterpret_cast<const uint4*>(line[i] + w);
+        const uint4 v = *reinterpret_cast<const uint4*>(ldca + line[i] + w);
         u.x &= v.x; u.y &= v.y; u.z &= v.z; u.w &= v.w;
       }
       ones += __popc(u.x) + __popc(u.y) + __popc(u.z) + __popc(u.w);
     }
   } else {
     for (uint32_t w = 0; w < wpl; ++w) {
-      uint32_t u = line[0][w];
-      for (uint32_t i = 1; i < d.lr; ++i) u &= line[i][w];
+      uint32_t u = ldca[line[0] + w];
+      for (uint32_t i = 1; i < d.lr; ++i) u &= ldca[line[i] + w];
       ones += __popc(u);
     }
   }
@@ -88,7 +120,8 @@ __device__ __forceinline__ void keep_host(uint32_t ip, uint32_t z0, uint32_t z_t
 // One complete, consistent tuple: count it against the join bound and queue
 // its IP for the warp's LDCA test (tested here when the queue is full).
 // Returns false when the detect must stop (a bound was hit).
-__device__ __forceinline__ bool emit_lp(const DevParams& d, const uint32_t* __restrict__ ldca,
+template <bool kSliding>
+__device__ __forceinline__ bool emit_lp(const DevParams& d, const LdcaRead& ldca,
                                         uint32_t rp, uint32_t lp, uint32_t z_theta,
                                         const Found& f, uint32_t& join_local,
                                         uint32_t* queue, uint32_t* queue_n) {
@@ -100,7 +133,7 @@ __device__ __forceinline__ bool emit_lp(const DevParams& d, const uint32_t* __re
   const uint32_t ip = (uint32_t)(((uint64_t)lp << d.r) | rp);
   const uint32_t at = atomicAdd(queue_n, 1u);
   if (at < (uint32_t)kHostQueue) queue[at] = ip;
-  else keep_host(ip, ldc_zeros(d, ldca, ip), z_theta, f);
+  else keep_host(ip, ldc_zeros<kSliding>(d, ldca, ip), z_theta, f);
   return true;
 }
 
@@ -108,15 +141,11 @@ __device__ __forceinline__ bool emit_lp(const DevParams& d, const uint32_t* __re
 // lines of wpl words are split over the lanes: with wpl >= 32 each lane
 // takes every 32nd word of each line and two hosts go per pass; with
 // wpl < 32 a pass takes 32 / wpl hosts, one word per lane.
-__device__ void test_queue(const DevParams& d, const uint32_t* __restrict__ ldca, const uint32_t* queue,
+template <bool kSliding>
+__device__ void test_queue(const DevParams& d, const LdcaRead& ldca, const uint32_t* queue,
                            uint32_t n, uint32_t z_theta, const Found& f, uint32_t lane) {
   const uint32_t wpl = 1u << (d.k_log2 - 5u);
-  const uint32_t cshift = 32u - d.lc_log2;
   const uint32_t k = 1u << d.k_log2;
-  auto line_of = [&](uint32_t ip, uint32_t i) {
-    const uint32_t col = (uint32_t)((uint64_t)mas(d.ha[2 + i], d.hb[2 + i], ip) >> cshift);
-    return ldca + ((uint64_t)((i << d.lc_log2) | col) << (d.k_log2 - 5u));
-  };
   if (wpl >= 32) {
     for (uint32_t q = 0; q < n; q += 2) {
       const bool two = q + 1 < n;
@@ -125,8 +154,8 @@ __device__ void test_queue(const DevParams& d, const uint32_t* __restrict__ ldca
       for (uint32_t w = lane; w < wpl; w += 32) {
         uint32_t u0 = kFull, u1 = kFull;
         for (uint32_t i = 0; i < d.lr; ++i) {
-          u0 &= line_of(ip0, i)[w];
-          u1 &= line_of(ip1, i)[w];
+          u0 &= ldc_word<kSliding>(ldca, ldc_line(d, ip0, i) + w);
+          u1 &= ldc_word<kSliding>(ldca, ldc_line(d, ip1, i) + w);
         }
         ones0 += __popc(u0);
         ones1 += __popc(u1);
@@ -150,7 +179,7 @@ __device__ void test_queue(const DevParams& d, const uint32_t* __restrict__ ldca
       if (q < n) {
         const uint32_t ip = queue[q];
         uint32_t u = kFull;
-        for (uint32_t i = 0; i < d.lr; ++i) u &= line_of(ip, i)[w];
+        for (uint32_t i = 0; i < d.lr; ++i) u &= ldc_word<kSliding>(ldca, ldc_line(d, ip, i) + w);
         ones = __popc(u);
       }
       for (uint32_t o = wpl >> 1; o > 0; o >>= 1) ones += __shfl_xor_sync(kFull, ones, o);
@@ -159,10 +188,15 @@ __device__ void test_queue(const DevParams& d, const uint32_t* __restrict__ ldca
   }
 }
 
+template <bool kSliding>
 __global__ void __launch_bounds__(kDetectThreads)
-k_detect(DevParams d, const uint8_t* __restrict__ seav, const uint32_t* __restrict__ ldca,
-         uint32_t z_theta, Found f) {
+k_detect(DevParams d, const uint8_t* __restrict__ seav, LdcaRead ldca, const uint64_t* __restrict__ clock,
+         uint32_t k_slices, uint32_t z_theta, Found f) {
   extern __shared__ uint32_t s_dyn[];
+  if (kSliding) {                                   // the window of the router's current slice
+    ldca.cur4 = ((uint32_t)(*clock % 255u) + 1u) * 0x01010101u;
+    ldca.k4 = k_slices * 0x01010101u;
+  }
   __shared__ uint32_t s_queue_n[kDetectWarps];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   uint32_t* queue = s_dyn + warp * kHostQueue;           // [kDetectWarps][kHostQueue] IPs
@@ -234,7 +268,7 @@ k_detect(DevParams d, const uint8_t* __restrict__ seav, const uint32_t* __restri
           start = 2;
         }
         if (start == d.sr) {
-          if (!emit_lp(d, ldca, rp, kv, z_theta, f, join_local, queue, queue_n)) stop = true;
+          if (!emit_lp<kSliding>(d, ldca, rp, kv, z_theta, f, join_local, queue, queue_n)) stop = true;
           continue;
         }
         uint32_t pos[8], skm[8], skv[8], sseu[8];
@@ -250,7 +284,7 @@ k_detect(DevParams d, const uint8_t* __restrict__ seav, const uint32_t* __restri
           const uint32_t s2 = sseu[dd] & sea[d.row_off[dd] + c];
           if (((v ^ skv[dd]) & d.cover[dd] & skm[dd]) == 0u && __popc(s2) >= 3) {
             if (dd == (int)d.sr - 1) {
-              if (!emit_lp(d, ldca, rp, skv[dd] | v, z_theta, f, join_local, queue, queue_n)) stop = true;
+              if (!emit_lp<kSliding>(d, ldca, rp, skv[dd] | v, z_theta, f, join_local, queue, queue_n)) stop = true;
               ++pos[dd];
             } else {
               const int nx = dd + 1;
@@ -266,7 +300,7 @@ k_detect(DevParams d, const uint8_t* __restrict__ seav, const uint32_t* __restri
     __syncwarp();
     // 3. the warp's LDCA test of this SEA's complete tuples
     const uint32_t nq = min(*queue_n, (uint32_t)kHostQueue);
-    if (nq) test_queue(d, ldca, queue, nq, z_theta, f, lane);
+    if (nq) test_queue<kSliding>(d, ldca, queue, nq, z_theta, f, lane);
     __syncwarp();
     if (lane == 0) *queue_n = 0;
     __syncwarp();
@@ -382,24 +416,44 @@ k_sort_emit(uint64_t* keys, uint32_t cap, const DetectStatus* status, const doub
 
 }  // namespace
 
-cudaError_t launch_detect(const DevParams& d, const uint8_t* seav, const uint32_t* ldca,
-                          uint32_t z_theta, uint64_t* keys, uint32_t cap, uint64_t max_join,
+namespace {
+
+template <bool kSliding>
+cudaError_t detect_launch(const DevParams& d, const uint8_t* seav, const LdcaRead& ldca, const uint64_t* clock,
+                          uint32_t k_slices, uint32_t z_theta, uint64_t* keys, uint32_t cap, uint64_t max_join,
                           DetectStatus* status, cudaStream_t s) {
   const size_t smem = (size_t)kDetectWarps * kHostQueue * sizeof(uint32_t) +
                       (size_t)kDetectWarps * d.sea_bytes * sizeof(uint16_t);
-  cudaError_t e = cudaFuncSetAttribute(k_detect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_detect<kSliding>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_detect, kDetectThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_detect<kSliding>, kDetectThreads, smem);
   if (per_sm < 1) per_sm = 1;
   const uint64_t n_sea = 1ull << d.r;
   uint64_t grid = (n_sea + kDetectWarps - 1) / kDetectWarps;
   if (grid > (uint64_t)sms * per_sm) grid = (uint64_t)sms * per_sm;
   Found f{keys, cap, max_join, status};
-  k_detect<<<(unsigned)grid, kDetectThreads, smem, s>>>(d, seav, ldca, z_theta, f);
+  k_detect<kSliding><<<(unsigned)grid, kDetectThreads, smem, s>>>(d, seav, ldca, clock, k_slices, z_theta, f);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_detect(const DevParams& d, const uint8_t* seav, const uint32_t* ldca,
+                          uint32_t z_theta, uint64_t* keys, uint32_t cap, uint64_t max_join,
+                          DetectStatus* status, cudaStream_t s) {
+  return detect_launch<false>(d, seav, LdcaRead{ldca, nullptr, 0u, 0u}, nullptr, 0u, z_theta, keys, cap, max_join,
+                              status, s);
+}
+
+cudaError_t launch_detect_sliding(const DevParams& d, const uint8_t* seav, const uint32_t* ldca,
+                                  const uint8_t* st_ldca, const uint64_t* clock, uint32_t k, uint32_t z_theta,
+                                  uint64_t* keys, uint32_t cap, uint64_t max_join, DetectStatus* status,
+                                  cudaStream_t s) {
+  const LdcaRead a{ldca, reinterpret_cast<const uint4*>(st_ldca), 0u, 0u};
+  return detect_launch<true>(d, seav, a, clock, k, z_theta, keys, cap, max_join, status, s);
 }
 
 cudaError_t launch_sort_emit(uint64_t* keys, uint32_t cap, const DetectStatus* status,

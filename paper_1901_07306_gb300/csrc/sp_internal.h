@@ -121,6 +121,31 @@ cudaError_t launch_scan_binned(const DevParams& d, uint8_t* seav, uint32_t* ldca
                                uint64_t n_pairs, const BinnedScratch& s, cudaStream_t st);
 // ldca |= transpose(planes)
 cudaError_t launch_fold(const DevParams& d, const uint32_t* planes, uint32_t* ldca, int grid, cudaStream_t st);
+// Sliding window stamps (Sec. 5.2): one byte per bit holding the id of the
+// last slice that set it, id(t) = t mod 255 + 1 (0 = never set).  Byte j of
+// active_mask4 is 0xFF iff byte j of s is an active stamp: non-zero, of age
+// (cur - stamp) mod 255 below k (byte-wise SIMD: d = cur - s mod 256, and
+// age = d - 1 where cur < s, the mod-255 wrap).  cur4 and k4 hold cur and k
+// in every byte (k <= 128).
+__device__ __forceinline__ uint32_t active_mask4(uint32_t s, uint32_t cur4, uint32_t k4) {
+  const uint32_t d = __vsub4(cur4, s);
+  const uint32_t age = __vadd4(d, __vcmpltu4(cur4, s));       // + 0xFF = - 1 where cur < s
+  return __vcmpltu4(age, k4) & ~__vcmpeq4(s, 0u);
+}
+
+// The same test as 4 bits (bit j for byte j): the four partial products of
+// the multiply land on distinct bits 21..24, so nothing carries.
+__device__ __forceinline__ uint32_t active4(uint32_t s, uint32_t cur4, uint32_t k4) {
+  return (((active_mask4(s, cur4, k4) & 0x01010101u) * 0x00204081u) >> 21) & 0xFu;
+}
+
+// The 32 active bits of one sketch word from its 32 stamps (two uint4).
+__device__ __forceinline__ uint32_t active32(const uint4& a, const uint4& b, uint32_t cur4, uint32_t k4) {
+  return active4(a.x, cur4, k4) | active4(a.y, cur4, k4) << 4 | active4(a.z, cur4, k4) << 8 |
+         active4(a.w, cur4, k4) << 12 | active4(b.x, cur4, k4) << 16 | active4(b.y, cur4, k4) << 20 |
+         active4(b.z, cur4, k4) << 24 | active4(b.w, cur4, k4) << 28;
+}
+
 // sliding window (sp_slide.cu); a sketch region is nw 32-bit words, word i
 // owning the 32 stamps [32 i, 32 i + 32) of its stamp region; `clock` is the
 // router's slice counter t in device memory (slice id t mod 255 + 1)
@@ -140,6 +165,13 @@ cudaError_t launch_merge(uint8_t* dst, const uint8_t* const* srcs, uint32_t n_sr
 cudaError_t launch_detect(const DevParams& d, const uint8_t* seav, const uint32_t* ldca,
                           uint32_t z_theta, uint64_t* keys, uint32_t cap, uint64_t max_join,
                           DetectStatus* status, cudaStream_t s);
+// The detect of a sliding router: seav is its window SEAV; an LDCA bit is in
+// the window iff its stamp (st_ldca, one byte per bit) is active at the
+// router's clock or it is set in the slice sketch ldca (not yet committed).
+cudaError_t launch_detect_sliding(const DevParams& d, const uint8_t* seav, const uint32_t* ldca,
+                                  const uint8_t* st_ldca, const uint64_t* clock, uint32_t k, uint32_t z_theta,
+                                  uint64_t* keys, uint32_t cap, uint64_t max_join, DetectStatus* status,
+                                  cudaStream_t s);
 cudaError_t launch_sort_emit(uint64_t* keys, uint32_t cap, const DetectStatus* status,
                              const double* est_table, uint32_t k_log2,
                              sp_candidate* out, cudaStream_t s);

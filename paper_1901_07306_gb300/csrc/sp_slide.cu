@@ -16,10 +16,12 @@
 //                 bit sketch and clears the sketch (one pass over the sketch;
 //                 counters of clear bits keep their stamp).  It runs when the
 //                 slice closes and before a merge reads the counters.
-//   k_commit_window  the same commit fused with one streaming pass over all
+//   k_commit_window  the same commit fused with one streaming pass over the
 //                 counters that writes the window's bits (active counters) as
-//                 an ordinary SEAV/LDCA: the detect of Sec. 3.2-3.3 and the
-//                 export read that image.
+//                 an ordinary SEAV/LDCA.  Export reads that image.  A detect
+//                 runs it over the SEAV alone: its LDCA test reads the stamps
+//                 of the tested hosts' lines (k_detect), and the slice's LDCA
+//                 bits are committed when the slice closes.
 //   k_clean       at every slide, one of M = 255 - k segments of the counter
 //                 pool is swept and counters of age >= k are reset to 0; each
 //                 counter is swept at most M slices after it expired, so its
@@ -45,21 +47,6 @@ __device__ __forceinline__ uint32_t slice_id(const uint64_t* clock) { return (ui
 
 __device__ __forceinline__ uint32_t age_of(uint32_t stamp, uint32_t cur) {
   return cur >= stamp ? cur - stamp : cur + 255u - stamp;
-}
-
-// Four stamps at once: byte j of the result is 0xFF iff byte j of s is an
-// active stamp (non-zero, age (cur - stamp) mod 255 below k).  Byte-wise
-// SIMD: d = cur - s mod 256, and age = d - 1 where cur < s (the mod-255 wrap).
-__device__ __forceinline__ uint32_t active_mask4(uint32_t s, uint32_t cur4, uint32_t k4) {
-  const uint32_t d = __vsub4(cur4, s);
-  const uint32_t age = __vadd4(d, __vcmpltu4(cur4, s));       // + 0xFF = - 1 where cur < s
-  return __vcmpltu4(age, k4) & ~__vcmpeq4(s, 0u);
-}
-
-// The same test as 4 bits (bit j for byte j): the four partial products of
-// the multiply land on distinct bits 21..24, so nothing carries.
-__device__ __forceinline__ uint32_t active4(uint32_t s, uint32_t cur4, uint32_t k4) {
-  return (((active_mask4(s, cur4, k4) & 0x01010101u) * 0x00204081u) >> 21) & 0xFu;
 }
 
 // Segment (t mod M) of a router's stamps, M = 255 - k, of units16 16-byte
