@@ -112,6 +112,12 @@ struct sp_ctx {
   sp::BinnedScratch bs;
   uint32_t** planes = nullptr;              // [n_routers], lazily allocated
   bool* planes_dirty = nullptr;             // bits not yet folded into the LDCA
+  // ldca_zero[r]: since r's last zeroing only binned rounds wrote its LDCA
+  // (discrete contexts), so the next fold may write the planes without
+  // reading the LDCA -- unless a binning launch spilled a bit past a full
+  // list, which sets the device flag ovf[r] (cleared with the zeroing)
+  bool* ldca_zero = nullptr;
+  uint32_t* ovf = nullptr;
   // sliding window (Sec. 5): one stamp byte per bit, per-router slice clock;
   // the bit sketch of a sliding router holds the current slice's bits until
   // they are committed to the stamps
@@ -345,6 +351,8 @@ void sp_destroy(sp_ctx* ctx) {
   cudaFree(ctx->window);
   cudaFree(ctx->bs.lists);
   cudaFree(ctx->bs.counts);
+  cudaFree(ctx->ovf);
+  free(ctx->ldca_zero);
   cudaFree(ctx->sketches);
   cudaFree(ctx->keys);
   cudaFree(ctx->records);
@@ -405,6 +413,7 @@ int sp_create(const sp_params* p, void* cuda_stream, sp_ctx** out) {
       cudaMalloc(&c->records, (uint64_t)c->cap * sizeof(sp_candidate)) != cudaSuccess ||
       cudaMalloc(&c->status, sizeof(DetectStatus)) != cudaSuccess ||
       cudaMalloc(&c->kerr, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&c->ovf, sizeof(uint32_t) * p->n_routers) != cudaSuccess ||
       cudaMalloc(&c->est_table, ((1ull << p->k_log2) + 1) * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     rc = SP_ERR_NOMEM;
@@ -422,7 +431,9 @@ int sp_create(const sp_params* p, void* cuda_stream, sp_ctx** out) {
       free(table);
     }
   }
-  if (rc == SP_OK && sp::launch_zero(c->sketches, c->stride * p->n_routers, c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
+  if (rc == SP_OK && sp::launch_zero_flags(c->sketches, c->stride * p->n_routers, c->ovf, p->n_routers, c->stream) !=
+                         cudaSuccess)
+    rc = SP_ERR_CUDA;
   if (rc == SP_OK && cudaMemsetAsync(c->status, 0, sizeof(DetectStatus), c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
   if (rc == SP_OK && cudaMemsetAsync(c->kerr, 0, sizeof(uint32_t), c->stream) != cudaSuccess) rc = SP_ERR_CUDA;
   if (rc == SP_OK) {
@@ -430,9 +441,12 @@ int sp_create(const sp_params* p, void* cuda_stream, sp_ctx** out) {
     c->multi_grid = sp::multi_max_grid(c->multi_threads);
     c->planes = static_cast<uint32_t**>(calloc(p->n_routers, sizeof(uint32_t*)));
     c->planes_dirty = static_cast<bool*>(calloc(p->n_routers, sizeof(bool)));
+    c->ldca_zero = static_cast<bool*>(calloc(p->n_routers, sizeof(bool)));
+    if (c->ldca_zero && p->window_slices <= 1)
+      for (uint32_t r = 0; r < p->n_routers; ++r) c->ldca_zero[r] = true;
     c->slice = static_cast<uint64_t*>(calloc(p->n_routers, sizeof(uint64_t)));
     c->slice_dirty = static_cast<bool*>(calloc(p->n_routers, sizeof(bool)));
-    if (!c->planes || !c->planes_dirty || !c->slice || !c->slice_dirty) rc = SP_ERR_NOMEM;
+    if (!c->planes || !c->planes_dirty || !c->slice || !c->slice_dirty || !c->ldca_zero) rc = SP_ERR_NOMEM;
   }
   if (rc == SP_OK && p->window_slices > 1) {
     c->sliding = true;
@@ -474,9 +488,12 @@ int sp_get_params(const sp_ctx* ctx, sp_params* out) {
 // Folds a router's pending binned-scan planes into its LDCA.
 static int fold_router(sp_ctx* ctx, uint32_t router) {
   if (!ctx->planes_dirty[router]) return SP_OK;
-  if (sp::launch_fold(ctx->d, ctx->planes[router], ctx->ldca(router), ctx->bs.fold_grid, ctx->stream) != cudaSuccess)
+  const uint32_t* fresh = ctx->ldca_zero[router] ? ctx->ovf + router : nullptr;
+  if (sp::launch_fold(ctx->d, ctx->planes[router], ctx->ldca(router), ctx->bs.fold_grid, ctx->stream, fresh) !=
+      cudaSuccess)
     return SP_ERR_CUDA;
   ctx->planes_dirty[router] = false;
+  ctx->ldca_zero[router] = false;
   return SP_OK;
 }
 
@@ -537,6 +554,7 @@ static sp::BinnedScratch binned_scratch(const sp_ctx* ctx, uint32_t router) {
   sp::BinnedScratch s = ctx->bs;
   s.planes = ctx->planes[router];
   s.accumulate = ctx->planes_dirty[router];
+  s.ovf = ctx->ovf + router;
   return s;
 }
 
@@ -552,6 +570,7 @@ static int do_update(sp_ctx* ctx, uint32_t router, const uint32_t* dev_pairs, ui
     ctx->planes_dirty[router] = true;
     return SP_OK;
   }
+  ctx->ldca_zero[router] = false;
   return sp::launch_scan(ctx->d, ctx->seav(router), ctx->ldca(router), dev_pairs, n_pairs,
                          ctx->scan_grid, ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
 }
@@ -611,7 +630,10 @@ int sp_reset(sp_ctx* ctx, uint32_t router) {
     if (cudaMemsetAsync(ctx->dev_clock(router), 0, sizeof(uint64_t), ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
     if (sp::launch_zero(ctx->st_seav(router), ctx->st_stride, ctx->stream) != cudaSuccess) return SP_ERR_CUDA;
   }
-  return sp::launch_zero(ctx->seav(router), ctx->stride, ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+  if (sp::launch_zero_flags(ctx->seav(router), ctx->stride, ctx->ovf + router, 1, ctx->stream) != cudaSuccess)
+    return SP_ERR_CUDA;
+  ctx->ldca_zero[router] = !ctx->sliding;
+  return SP_OK;
 }
 
 int sp_reset_range(sp_ctx* ctx, uint32_t first, uint32_t count) {
@@ -625,12 +647,16 @@ int sp_reset_range(sp_ctx* ctx, uint32_t first, uint32_t count) {
     }
     return SP_OK;
   }
+  // the routers' regions are contiguous: one zeroing launch for all of them
+  if (sp::launch_zero_flags(ctx->seav(first), ctx->stride * count, ctx->ovf + first, count, ctx->stream) !=
+      cudaSuccess)
+    return SP_ERR_CUDA;
   for (uint32_t r = first; r < first + count; ++r) {
     ctx->planes_dirty[r] = false;                // pending planes belong to the old window
     ctx->slice_dirty[r] = false;
+    ctx->ldca_zero[r] = true;
   }
-  // the routers' regions are contiguous: one zeroing launch for all of them
-  return sp::launch_zero(ctx->seav(first), ctx->stride * count, ctx->stream) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+  return SP_OK;
 }
 
 int sp_update(sp_ctx* ctx, uint32_t router, const uint32_t* dev_pairs, uint64_t n_pairs) {
@@ -812,6 +838,7 @@ int sp_update_batched(sp_ctx* ctx, uint32_t n_batches, const uint32_t* routers,
   for (uint32_t r = 0; r < R; ++r) {
     if (total[r] == 0) continue;
     if (!use_binned(ctx, total[r])) {
+      ctx->ldca_zero[r] = false;                         // direct form: bits straight into the LDCA
       for (uint32_t q = first[r]; q < first[r + 1]; ++q)
         rest.push_back(sp_batch{dev_pairs[order[q]], n_pairs[order[q]], r, 0u});
       continue;
@@ -899,7 +926,10 @@ int sp_update_batched_device(sp_ctx* ctx, const sp_batch* dev_batches, uint32_t 
   if (n_batches == 0) return SP_OK;
   if (!dev_batches || n_batches > 8192) return SP_ERR_PARAM;
   // the table is read on the device: any router may receive bits
-  for (uint32_t r = 0; r < ctx->p.n_routers; ++r) ctx->slice_dirty[r] = true;
+  for (uint32_t r = 0; r < ctx->p.n_routers; ++r) {
+    ctx->slice_dirty[r] = true;
+    ctx->ldca_zero[r] = false;
+  }
   return launch_table(ctx, dev_batches, n_batches);
 }
 
@@ -908,6 +938,7 @@ int sp_autotune(sp_ctx* ctx, const uint32_t* dev_pairs, uint64_t n_pairs, uint32
   if (!ctx || !dev_pairs || n_pairs == 0 || ((uintptr_t)dev_pairs & 7u)) return SP_ERR_PARAM;
   const sp_batch one{dev_pairs, n_pairs, 0u, 0u};
   const sp_batch* dev_tab = nullptr;
+  ctx->ldca_zero[0] = false;                          // the trial scans write router 0 directly
   int rc = upload_table(ctx, &one, 1, &dev_tab);
   if (rc != SP_OK) return rc;
   int dev = 0, sms = 0;
@@ -1022,6 +1053,7 @@ int sp_merge(sp_ctx* ctx, const uint32_t* routers, uint32_t n, uint32_t dst_rout
   if (dst_router >= ctx->p.n_routers) return SP_ERR_ROUTER;
   for (uint32_t i = 0; i < n; ++i)
     if (routers[i] >= ctx->p.n_routers) return SP_ERR_ROUTER;
+  ctx->ldca_zero[dst_router] = false;
   std::vector<const uint8_t*> srcs;                // every listed router but dst (x | x = x)
   srcs.reserve(n);
   if (ctx->sliding) {
@@ -1072,6 +1104,7 @@ int sp_merge_device(sp_ctx* ctx, const void* const* dev_images, uint32_t n, uint
   }
   const int rc = fold_router(ctx, dst_router);
   if (rc != SP_OK) return rc;
+  ctx->ldca_zero[dst_router] = false;
   return sp::launch_merge(ctx->seav(dst_router), srcs.data(), n, ctx->stride, ctx->stream) == cudaSuccess
              ? SP_OK : SP_ERR_CUDA;
 }
@@ -1241,6 +1274,7 @@ int sp_import(sp_ctx* ctx, uint32_t router, const void* host_buf, uint64_t n) {
       h.seav_bytes != ctx->seav_bytes || h.ldca_bytes != ctx->ldca_bytes)
     return SP_ERR_CHECKSUM;
   ctx->planes_dirty[router] = false;
+  ctx->ldca_zero[router] = false;
   if (cudaMemcpyAsync(ctx->seav(router), in + sizeof(h), ctx->seav_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
       cudaMemcpyAsync(ctx->ldca(router), in + sizeof(h) + ctx->seav_bytes, ctx->ldca_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
     return SP_ERR_CUDA;

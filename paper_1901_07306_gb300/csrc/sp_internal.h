@@ -89,10 +89,13 @@ struct BinnedScratch {
   uint64_t list_words = 0;      // hips the lists allocation holds
   uint64_t max_pairs = 0;       // pairs per binning round the lists are sized for
   int fold_grid = 0;
+  uint32_t* ovf = nullptr;      // the router's flag: set when a pair's LDCA bit bypassed the lists
 };
 
 // ---- launchers (return cudaGetLastError() of the launch) -------------------
 cudaError_t launch_zero(void* dev, uint64_t bytes, cudaStream_t s);
+// launch_zero, and flags[0, n_flags) = 0 in the same launch
+cudaError_t launch_zero_flags(void* dev, uint64_t bytes, uint32_t* flags, uint32_t n_flags, cudaStream_t s);
 cudaError_t launch_scan(const DevParams& d, uint8_t* seav, uint32_t* ldca,
                         const uint32_t* pairs, uint64_t n_pairs, int grid, cudaStream_t s);
 int scan_grid(const DevParams& d);
@@ -120,7 +123,12 @@ int binned_fold_grid();
 cudaError_t launch_scan_binned(const DevParams& d, uint8_t* seav, uint32_t* ldca, const uint32_t* pairs,
                                uint64_t n_pairs, const BinnedScratch& s, cudaStream_t st);
 // ldca |= transpose(planes)
-cudaError_t launch_fold(const DevParams& d, const uint32_t* planes, uint32_t* ldca, int grid, cudaStream_t st);
+// fresh: the router's flag (BinnedScratch::ovf) when its LDCA was zeroed
+// and nothing but binned rounds wrote it since; the fold then writes the
+// transposed planes without reading the LDCA, unless the flag is set.
+// nullptr: ldca |= transpose(planes).
+cudaError_t launch_fold(const DevParams& d, const uint32_t* planes, uint32_t* ldca, int grid, cudaStream_t st,
+                        const uint32_t* fresh = nullptr);
 // Sliding window stamps (Sec. 5.2): one byte per bit holding the id of the
 // last slice that set it, id(t) = t mod 255 + 1 (0 = never set).  Byte j of
 // active_mask4 is 0xFF iff byte j of s is an active stamp: non-zero, of age

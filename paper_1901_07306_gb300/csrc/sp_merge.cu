@@ -18,10 +18,12 @@ struct SrcList {
   const uint4* p[kMaxSrc];
 };
 
-__global__ void __launch_bounds__(kThreads) k_zero(uint4* __restrict__ p, uint64_t n16) {
+__global__ void __launch_bounds__(kThreads)
+k_zero(uint4* __restrict__ p, uint64_t n16, uint32_t* __restrict__ flags, uint32_t n_flags) {
   const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (uint64_t)gridDim.x * blockDim.x)
-    p[i] = z;
+  const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (uint64_t i = gid; i < n16; i += (uint64_t)gridDim.x * blockDim.x) p[i] = z;
+  for (uint64_t i = gid; i < n_flags; i += (uint64_t)gridDim.x * blockDim.x) flags[i] = 0u;
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -47,13 +49,18 @@ int stream_grid() {
 
 // bytes must be a multiple of 16 and the pointer 16-byte aligned (sketch
 // regions are padded to 256 bytes by the context).
-cudaError_t launch_zero(void* dev, uint64_t bytes, cudaStream_t s) {
+cudaError_t launch_zero_flags(void* dev, uint64_t bytes, uint32_t* flags, uint32_t n_flags, cudaStream_t s) {
   const uint64_t n16 = bytes / 16;
-  if (n16 == 0) return cudaSuccess;
-  uint64_t grid = (n16 + kThreads - 1) / kThreads;
+  const uint64_t work = n16 > n_flags ? n16 : n_flags;
+  if (work == 0) return cudaSuccess;
+  uint64_t grid = (work + kThreads - 1) / kThreads;
   if (grid > (uint64_t)stream_grid()) grid = stream_grid();
-  k_zero<<<(unsigned)grid, kThreads, 0, s>>>(reinterpret_cast<uint4*>(dev), n16);
+  k_zero<<<(unsigned)grid, kThreads, 0, s>>>(reinterpret_cast<uint4*>(dev), n16, flags, n_flags);
   return cudaGetLastError();
+}
+
+cudaError_t launch_zero(void* dev, uint64_t bytes, cudaStream_t s) {
+  return launch_zero_flags(dev, bytes, nullptr, 0u, s);
 }
 
 cudaError_t launch_merge(uint8_t* dst, const uint8_t* const* srcs, uint32_t n_src,

@@ -102,7 +102,7 @@ template <int THREADS, int STAGE, int TPR, int PER_SM>
 __global__ void __launch_bounds__(THREADS, PER_SM)
 k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
       BinSrc src, uint32_t* __restrict__ lists, uint32_t* __restrict__ counts, uint32_t cap,
-      bool append, uint32_t rot) {
+      bool append, uint32_t rot, uint32_t* __restrict__ ovf) {
   constexpr int TILE = THREADS * kVec * 2;
   constexpr int QUEUE = TPR * TILE / 32;              // sampled pairs per round: 4x the expected 2^-7
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -122,6 +122,12 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
   const uint32_t lane = tid & 31u;
   uint32_t lt_mask;                                // lanes below this one
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt_mask));
+  // a hip whose row or list was full: its LDCA bits go straight to L2, and
+  // the router's flag tells the fold that the LDCA is no longer all zero
+  auto spill = [&](uint32_t hip, uint32_t b) {
+    ldca_red(d, ldca, hip, b);
+    if (ovf) *ovf = 1u;
+  };
   // tiles of the streams, back to back: stream b owns tiles [s_tpref[b], s_tpref[b + 1])
   if (tid == 0) {
     uint64_t acc = 0;
@@ -208,7 +214,7 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
     if (__any_sync(kFull, over != 0u)) {
 #pragma unroll
       for (int q = 0; q < kGroup; ++q) {
-        if ((over >> q) & 1u) ldca_red(d, ldca, hip[q], bin[q]);
+        if ((over >> q) & 1u) spill(hip[q], bin[q]);
         if ((over >> (kGroup + q)) & 1u) seav_set(d, seav, hip[q], mas(d.ha[0], d.hb[0], oip[q]));
       }
     }
@@ -227,7 +233,7 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
         cur += kChunk;
       } else {                                      // list full: straight to L2
         const uint32_t h[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
-        for (int e = 0; e < 8; ++e) ldca_red(d, ldca, h[e], b);
+        for (int e = 0; e < 8; ++e) spill(h[e], b);
       }
     }
     const uint32_t rem = f - nch * kChunk;
@@ -326,22 +332,35 @@ k_bin(DevParams d, uint8_t* __restrict__ seav, uint32_t* __restrict__ ldca,
     for (uint32_t e = 0; e < f; ++e) {
       const uint32_t h = stage[b * STAGE + e];
       if (c < cap) list[c++] = h;
-      else ldca_red(d, ldca, h, b);
+      else spill(h, b);
     }
     counts[(uint64_t)b * G + cta] = c;
   }
 }
 
+// A list read once streams past L2 (evict first); a list that SPLIT > 1
+// blocks read, close together in time, stays there for the second read.
+template <int SPLIT>
+__device__ __forceinline__ uint32_t load_hip(const uint32_t* p) {
+  return SPLIT == 1 ? __ldcs(p) : __ldg(p);
+}
+
 // k_apply, LCL = log2 LC when it is fixed at compile time (profiles D, D3
-// and S: constant shifts and row offsets), 0 for any LC.
-template <int LR, int THREADS, int LCL>
+// and S: constant shifts and row offsets), 0 for any LC.  SPLIT blocks share
+// a plane, each holding LR / SPLIT of its LDCA rows in shared memory and
+// reading the whole hip list: wide planes (LC = 2^18: 128 KiB for four rows)
+// would otherwise leave one block per SM.
+template <int LR, int THREADS, int LCL, int SPLIT>
 __global__ void __launch_bounds__(THREADS)
 k_apply(DevParams d, const uint32_t* __restrict__ lists, const uint32_t* __restrict__ counts,
         uint32_t G, uint32_t cap, uint32_t* __restrict__ planes, bool accumulate) {
   extern __shared__ uint32_t s_plane[];
-  const uint32_t b = blockIdx.x;
+  constexpr int LRP = LR / SPLIT;                                  // rows of this block
+  const uint32_t b = blockIdx.x / SPLIT;
+  const uint32_t row0 = (blockIdx.x % SPLIT) * (uint32_t)LRP;
   const uint32_t lc_log2 = LCL ? (uint32_t)LCL : d.lc_log2;
-  const uint32_t words = ((uint32_t)LR << lc_log2) >> 5;          // plane words
+  const uint32_t words = ((uint32_t)LRP << lc_log2) >> 5;         // words of the block's rows
+  const uint32_t word0 = row0 << (lc_log2 - 5u);                  // their first plane word
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t nwarps = THREADS / 32;
   // LH_i(hip) = h >> cshift (5 <= lc_log2 <= 20): LDC h >> cshift of row i is
@@ -352,21 +371,24 @@ k_apply(DevParams d, const uint32_t* __restrict__ lists, const uint32_t* __restr
   // (w / 8) k 8 + 8 b + w mod 8, so that a 32-byte chunk holds 8 words of one plane
   const uint64_t chunk_stride = (uint64_t)(1u << d.k_log2) * 8u;
   uint32_t* dst = planes + (uint64_t)b * 8u;
-  auto at_word = [&](uint32_t w) { return dst + (uint64_t)(w >> 3) * chunk_stride + (w & 7u); };
+  auto at_word = [&](uint32_t w) {
+    w += word0;
+    return dst + (uint64_t)(w >> 3) * chunk_stride + (w & 7u);
+  };
   // the rows' hash words, held in registers
-  uint32_t a_lo[LR], a_hi[LR];
-  uint64_t bw[LR];
+  uint32_t a_lo[LRP], a_hi[LRP];
+  uint64_t bw[LRP];
 #pragma unroll
-  for (int r = 0; r < LR; ++r) {
-    a_lo[r] = (uint32_t)d.ha[2 + r];
-    a_hi[r] = (uint32_t)(d.ha[2 + r] >> 32);
-    bw[r] = d.hb[2 + r];
+  for (int r = 0; r < LRP; ++r) {
+    a_lo[r] = (uint32_t)d.ha[2 + row0 + r];
+    a_hi[r] = (uint32_t)(d.ha[2 + row0 + r] >> 32);
+    bw[r] = d.hb[2 + row0 + r];
   }
   for (uint32_t w = tid; w < words; w += THREADS) s_plane[w] = accumulate ? *at_word(w) : 0u;
   __syncthreads();
   auto set_bits = [&](uint32_t hip) {
 #pragma unroll
-    for (int r = 0; r < LR; ++r) {
+    for (int r = 0; r < LRP; ++r) {
       const uint64_t lo = (uint64_t)a_lo[r] * hip + bw[r];
       const uint32_t h = (uint32_t)(lo >> 32) + a_hi[r] * hip;      // MAS (Sec. 3.3 LH_r)
       if (LCL) {
@@ -386,7 +408,7 @@ k_apply(DevParams d, const uint32_t* __restrict__ lists, const uint32_t* __restr
     for (; i0 + 32 * kApplyUnroll <= n; i0 += 32 * kApplyUnroll) {     // whole rounds: no bounds checks
       uint32_t hip[kApplyUnroll];
 #pragma unroll
-      for (int u = 0; u < kApplyUnroll; ++u) hip[u] = __ldcs(src + i0 + u * 32);   // all loads in flight
+      for (int u = 0; u < kApplyUnroll; ++u) hip[u] = load_hip<SPLIT>(src + i0 + u * 32);   // all in flight
 #pragma unroll
       for (int u = 0; u < kApplyUnroll; ++u) set_bits(hip[u]);
     }
@@ -394,7 +416,7 @@ k_apply(DevParams d, const uint32_t* __restrict__ lists, const uint32_t* __restr
       uint32_t hip[kApplyUnroll];
 #pragma unroll
       for (int u = 0; u < kApplyUnroll; ++u)
-        hip[u] = (i0 + u * 32 + lane < n) ? __ldcs(src + i0 + u * 32) : 0u;
+        hip[u] = (i0 + u * 32 + lane < n) ? load_hip<SPLIT>(src + i0 + u * 32) : 0u;
 #pragma unroll
       for (int u = 0; u < kApplyUnroll; ++u)
         if (i0 + u * 32 + lane < n) set_bits(hip[u]);
@@ -424,7 +446,9 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, uint32_t lane) {
 // times 4 consecutive LDC words: it transposes 32 planes x 32 LDCs per word
 // and ORs the result into the lanes' LDC lines.
 __global__ void __launch_bounds__(256)
-k_fold(const uint32_t* __restrict__ planes, uint32_t* __restrict__ ldca, uint32_t W, uint32_t k_log2) {
+k_fold(const uint32_t* __restrict__ planes, uint32_t* __restrict__ ldca, uint32_t W, uint32_t k_log2,
+       const uint32_t* __restrict__ fresh) {
+  const bool write_only = fresh != nullptr && *fresh == 0u;       // the LDCA is all zero: no read
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t wpl = 1u << (k_log2 - 5u);                       // words per LDC
   const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -456,11 +480,11 @@ k_fold(const uint32_t* __restrict__ planes, uint32_t* __restrict__ ldca, uint32_
         for (int u = 0; u < 4; ++u) acc[u] = transpose32(x[u][j], lane);
         uint32_t* line = ldca + ((uint64_t)(J0 + j) * 32u + lane) * wpl;
         if (wpl >= 4) {
-          uint4 o = *reinterpret_cast<uint4*>(line + q0);
+          uint4 o = write_only ? make_uint4(0u, 0u, 0u, 0u) : *reinterpret_cast<uint4*>(line + q0);
           o.x |= acc[0]; o.y |= acc[1]; o.z |= acc[2]; o.w |= acc[3];
           *reinterpret_cast<uint4*>(line + q0) = o;
         } else {
-          for (uint32_t u = 0; u < wpl; ++u) line[u] |= acc[u];
+          for (uint32_t u = 0; u < wpl; ++u) line[u] = (write_only ? 0u : line[u]) | acc[u];
         }
       }
     }
@@ -472,7 +496,9 @@ k_fold(const uint32_t* __restrict__ planes, uint32_t* __restrict__ ldca, uint32_
 // sector into each of its 8 LDC lines; the 8 chunks of 8 planes' words are
 // loaded up front (16 loads in flight per lane).
 __global__ void __launch_bounds__(256)
-k_fold8(const uint32_t* __restrict__ planes, uint32_t* __restrict__ ldca, uint32_t W, uint32_t k_log2) {
+k_fold8(const uint32_t* __restrict__ planes, uint32_t* __restrict__ ldca, uint32_t W, uint32_t k_log2,
+        const uint32_t* __restrict__ fresh) {
+  const bool write_only = fresh != nullptr && *fresh == 0u;       // the LDCA is all zero: no read
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t wpl = 1u << (k_log2 - 5u);                       // words per LDC, >= 8
   const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -497,7 +523,11 @@ k_fold8(const uint32_t* __restrict__ planes, uint32_t* __restrict__ ldca, uint32
     for (int j = 0; j < 8; ++j) {
       if ((uint32_t)j >= nj) break;
       uint4* line = reinterpret_cast<uint4*>(ldca + ((uint64_t)(J0 + j) * 32u + lane) * wpl + q0);
-      uint4 o0 = line[0], o1 = line[1];
+      uint4 o0 = make_uint4(0u, 0u, 0u, 0u), o1 = o0;
+      if (!write_only) {
+        o0 = line[0];
+        o1 = line[1];
+      }
       o0.x |= transpose32(x[0][j], lane); o0.y |= transpose32(x[1][j], lane);
       o0.z |= transpose32(x[2][j], lane); o0.w |= transpose32(x[3][j], lane);
       o1.x |= transpose32(x[4][j], lane); o1.y |= transpose32(x[5][j], lane);
@@ -518,28 +548,28 @@ cudaError_t bin_chunk(const DevParams& d, uint8_t* seav, uint32_t* ldca, const B
   auto kern = k_bin<THREADS, STAGE, TPR, PER_SM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
   if (e != cudaSuccess) return e;
-  kern<<<s.ctas, THREADS, bin_smem, st>>>(d, seav, ldca, src, s.lists, s.counts, cap, append, rot);
+  kern<<<s.ctas, THREADS, bin_smem, st>>>(d, seav, ldca, src, s.lists, s.counts, cap, append, rot, s.ovf);
   return cudaGetLastError();
 }
 
-template <int LR, int THREADS, int LCL>
+template <int LR, int THREADS, int LCL, int SPLIT = 1>
 cudaError_t apply_round_t(const DevParams& d, const BinnedScratch& s, uint32_t cap, bool accumulate, cudaStream_t st) {
   const uint32_t bins = 1u << d.k_log2;
-  const uint32_t words = ((uint32_t)LR << d.lc_log2) >> 5;
+  const uint32_t words = ((uint32_t)(LR / SPLIT) << d.lc_log2) >> 5;
   const size_t apply_smem = (size_t)words * sizeof(uint32_t);
-  auto kern = k_apply<LR, THREADS, LCL>;
+  auto kern = k_apply<LR, THREADS, LCL, SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_smem);
   if (e != cudaSuccess) return e;
-  kern<<<bins, THREADS, apply_smem, st>>>(d, s.lists, s.counts, s.ctas, cap, s.planes, accumulate);
+  kern<<<bins * SPLIT, THREADS, apply_smem, st>>>(d, s.lists, s.counts, s.ctas, cap, s.planes, accumulate);
   return cudaGetLastError();
 }
 
 template <int LR, int THREADS>
 cudaError_t apply_round_lc(const DevParams& d, const BinnedScratch& s, uint32_t cap, bool accumulate,
                            cudaStream_t st) {
-  if (LR == 4) {                      // the profiles' LDCA widths get constant shifts
+  if constexpr (LR == 4) {            // the profiles' LDCA widths get constant shifts
     if (d.lc_log2 == 16) return apply_round_t<LR, THREADS, 16>(d, s, cap, accumulate, st);
-    if (d.lc_log2 == 18) return apply_round_t<LR, THREADS, 18>(d, s, cap, accumulate, st);
+    if (d.lc_log2 == 18) return apply_round_t<LR, THREADS, 18, 2>(d, s, cap, accumulate, st);
     if (d.lc_log2 == 14) return apply_round_t<LR, THREADS, 14>(d, s, cap, accumulate, st);
   }
   return apply_round_t<LR, THREADS, 0>(d, s, cap, accumulate, st);
@@ -597,10 +627,11 @@ int binned_ctas(const BinShape& shape) { return sm_count() * (int)shape.per_sm; 
 
 int binned_fold_grid() { return sm_count() * 8; }
 
-cudaError_t launch_fold(const DevParams& d, const uint32_t* planes, uint32_t* ldca, int grid, cudaStream_t st) {
+cudaError_t launch_fold(const DevParams& d, const uint32_t* planes, uint32_t* ldca, int grid, cudaStream_t st,
+                        const uint32_t* fresh) {
   const uint32_t words = (uint32_t)(((uint64_t)d.lr << d.lc_log2) >> 5);
-  if (d.k_log2 >= 8) k_fold8<<<grid, 256, 0, st>>>(planes, ldca, words, d.k_log2);
-  else k_fold<<<grid, 256, 0, st>>>(planes, ldca, words, d.k_log2);
+  if (d.k_log2 >= 8) k_fold8<<<grid, 256, 0, st>>>(planes, ldca, words, d.k_log2, fresh);
+  else k_fold<<<grid, 256, 0, st>>>(planes, ldca, words, d.k_log2, fresh);
   return cudaGetLastError();
 }
 

@@ -484,3 +484,59 @@ def test_random_profiles_both_scan_forms(sp, torch, case):
             if not overflow:
                 assert n == n_want and rc in (sp.SP_OK, sp.SP_ERR_TRUNCATED)
                 assert_same_results(got, want[:len(got)])
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_wide_planes_two_blocks_per_plane(sp, torch, mode):
+    """LC = 2^18 (profile D3): a binned plane of four rows is 128 KiB, so two
+    blocks share each plane, two rows apiece.  In the binned form three
+    updates (one of 4,099 pairs) accumulate into the planes before the fold;
+    in both forms the sketch and the detection equal the oracle's."""
+    kw = dict(r=16, isb=(0, 4, 8, 12), ibn=(7, 7, 7, 7), lc_log2=18, theta=256, seed=31, scan_mode=mode)
+    a, _ = W.single_window(seed=31, n=(1 << 20) + 3, n_background=1 << 15, n_planted=6, planted_degree=900)
+    b, _ = W.single_window(seed=32, n=(1 << 19) + 5, n_background=1 << 14, n_planted=6, planted_degree=700)
+    c = W.uniform_pairs(4099, seed=33, n_hosts=300)
+    with sp.SuperPoint(**kw) as ctx:
+        ctx.update(dev(torch, a))
+        ctx.update(dev(torch, c))
+        ctx.update(dev(torch, b, 1))
+        osk = O.Sketch(oracle_params(kw)).update(np.concatenate([a, c, b]))
+        assert_same_sketch(ctx, osk)
+        got, n, rc = ctx.detect()
+        want, n_want, _ = osk.detect()
+        assert rc == sp.SP_OK and n == n_want
+        assert_same_results(got, want)
+
+
+def test_fold_of_a_freshly_zeroed_ldca(sp, torch):
+    """After a reset the fold writes the binned planes without reading the
+    LDCA.  It must still OR whenever something else wrote the LDCA first: a
+    binning launch that spilled past a full list, a merge into the router, an
+    import, a direct update.  Each case against the oracle."""
+    n = 1 << 19
+    rng = np.random.default_rng(41)
+    skew = np.stack([rng.integers(0, 2**32, n, dtype=np.uint32), np.full(n, 0x0A000001, np.uint32)], 1)
+    a = W.uniform_pairs(1 << 18, seed=41, n_hosts=20000)
+    b = W.uniform_pairs(1 << 18, seed=42, n_hosts=30000)
+    kw = dict(seed=41, n_routers=4, scan_mode=2)
+    op = oracle_params(kw)
+    with sp.SuperPoint(**kw) as ctx:
+        ctx.update(dev(torch, skew), router=0)                 # lists overflow: spilled bits in the LDCA
+        ctx.update(dev(torch, a), router=1)
+        assert_same_sketch(ctx, O.Sketch(op).update(skew), router=0)
+        assert_same_sketch(ctx, O.Sketch(op).update(a), router=1)
+        ctx.merge([1], 2)                                      # router 2's LDCA now holds a's bits
+        ctx.update(dev(torch, b), router=2)
+        assert_same_sketch(ctx, O.Sketch(op).update(a).update(b), router=2)
+        image = sp.sp_export(ctx.ctx, 1)
+        sp.sp_reset_range(ctx.ctx, 0, 4)                       # every router fresh again
+        ctx.update(dev(torch, b), router=0)                    # no spill this time
+        assert_same_sketch(ctx, O.Sketch(op).update(b), router=0)
+        assert sp.sp_import(ctx.ctx, 3, image) == sp.SP_OK     # router 3 = a's sketch
+        ctx.update(dev(torch, b), router=3)
+        assert_same_sketch(ctx, O.Sketch(op).update(a).update(b), router=3)
+    with sp.SuperPoint(**dict(kw, scan_mode=0)) as ctx:        # auto: a small direct update, then a binned one
+        ctx.update(dev(torch, a[:4096]))
+        big = W.uniform_pairs((1 << 22) + 11, seed=43, n_hosts=1 << 20)
+        ctx.update(dev(torch, big))
+        assert_same_sketch(ctx, O.Sketch(oracle_params(dict(kw, scan_mode=0))).update(a[:4096]).update(big))
