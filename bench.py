@@ -904,7 +904,7 @@ def _line(leg, args, value, ms):
 def run_distributed(args):
     torch, sp, W = _device_setup()
     leg = distributed_leg(torch, sp, W, args.router_log2, args.batches_per_router, args.steps, args.warmup,
-                          with_accuracy=True)
+                          with_accuracy=not args.no_extra)
     print(json.dumps(_line(leg, args, leg["batched"]["value"], leg["batched"]["ms_per_step"])), flush=True)
     return 0
 
