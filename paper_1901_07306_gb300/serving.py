@@ -50,7 +50,7 @@ import torch
 @dataclass
 class Request:
     router: int
-    pairs: torch.Tensor          # pinned host int32 tensor of 2 n values
+    pairs: torch.Tensor          # int32 tensor of 2 n values: pinned host memory or CUDA
     arrival: float               # seconds after the start of the run
     window: int = -1
     t_ack: float = float("nan")
