@@ -189,7 +189,7 @@ __device__ void test_queue(const DevParams& d, const LdcaRead& ldca, const uint3
 }
 
 template <bool kSliding>
-__global__ void __launch_bounds__(kDetectThreads)
+__global__ void __launch_bounds__(kDetectThreads, 4)
 k_detect(DevParams d, const uint8_t* __restrict__ seav, LdcaRead ldca, const uint64_t* __restrict__ clock,
          uint32_t k_slices, uint32_t z_theta, Found f) {
   extern __shared__ uint32_t s_dyn[];
