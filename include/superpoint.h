@@ -475,11 +475,12 @@ SP_API int sp_import(sp_ctx* ctx, uint32_t router, const void* host_buf, uint64_
  * every GPU that loads the library until the process exits.  The first call
  * on each device sets the array up: it looks up the array's device address
  * (cudaGetSymbolAddress, with the device current) and writes the estimate
- * tables of every supported k into it with one synchronous copy.  Later
- * calls copy nothing from the host.  All calls on a device share the array and it keeps the last call's
- * contents (each call resets what must start from zero): calls that overlap
- * on the GPU -- on different streams, or from different host threads -- race
- * and give undefined results.  Errors: SP_ERR_PARAM (a limit above exceeded,
+ * tables of every supported k into it with one synchronous copy, so make that
+ * first call before any stream capture begins.  Later calls copy nothing
+ * from the host.  All calls on a device share the array and it keeps the
+ * last call's contents (each call resets what must start from zero): calls
+ * that overlap on the GPU -- on different streams, or from different host
+ * threads -- race and give undefined results.  Errors: SP_ERR_PARAM (a limit above exceeded,
  * invalid parameters, misaligned pointer), SP_ERR_CUDA; returns
  * SP_WARN_THETA_BELOW_INIT like sp_detect_async. */
 SP_API int sp_detect_noalloc(const sp_params* p, const uint8_t* dev_seav, const uint32_t* dev_ldca,
