@@ -43,6 +43,19 @@ constexpr int kDetectWarps = 8;
 constexpr int kDetectThreads = kDetectWarps * 32;
 constexpr int kHostQueue = 256;                  // complete tuples queued per warp
 constexpr uint32_t kFull = 0xFFFFFFFFu;
+// SEAs of 512 bytes (profiles D, D3 and S) are staged in shared memory: a
+// ring of kSeaRing SEAs per warp, filled kSeaRing - 1 SEAs ahead of use
+constexpr uint32_t kStagedSea = 512;
+constexpr int kSeaRing = 4;
+
+// 16-byte asynchronous copy from global to shared memory (one per lane)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
 
 struct Found {
   uint64_t* keys;
@@ -191,8 +204,8 @@ __device__ void test_queue(const DevParams& d, const LdcaRead& ldca, const uint3
 template <bool kSliding>
 __global__ void __launch_bounds__(kDetectThreads, 4)
 k_detect(DevParams d, const uint8_t* __restrict__ seav, LdcaRead ldca, const uint64_t* __restrict__ clock,
-         uint32_t k_slices, uint32_t z_theta, Found f) {
-  extern __shared__ uint32_t s_dyn[];
+         uint32_t k_slices, uint32_t z_theta, Found f, bool staged) {
+  extern __shared__ __align__(16) uint32_t s_dyn[];
   if (kSliding) {                                   // the window of the router's current slice
     ldca.cur4 = ((uint32_t)(*clock % 255u) + 1u) * 0x01010101u;
     ldca.k4 = k_slices * 0x01010101u;
@@ -205,14 +218,39 @@ k_detect(DevParams d, const uint8_t* __restrict__ seav, LdcaRead ldca, const uin
   if (lane == 0) *queue_n = 0;
   __syncwarp();
   const uint32_t n_sea = 1u << d.r;
+  const uint32_t stride = gridDim.x * kDetectWarps;
+  // staged SEAs (512 bytes, 16-byte aligned SEAV): the warp's ring of
+  // kSeaRing SEAs after the lists; 16 bytes per lane and SEA by cp.async,
+  // one commit group per SEA (empty past the last SEA, so that the count of
+  // groups in flight stays fixed)
+  uint8_t* ring = reinterpret_cast<uint8_t*>(s_dyn + kDetectWarps * kHostQueue) +
+                  (size_t)kDetectWarps * d.sea_bytes * sizeof(uint16_t) + (size_t)warp * kSeaRing * kStagedSea;
+  auto stage_sea = [&](uint32_t rp, uint32_t slot) {
+    if (rp < n_sea) cp_async16(ring + slot * kStagedSea + 16u * lane, seav + (uint64_t)rp * kStagedSea + 16u * lane);
+    cp_async_commit();
+  };
+  uint32_t rp = blockIdx.x * kDetectWarps + warp;
+  if (staged) {
+#pragma unroll
+    for (int j = 0; j < kSeaRing - 1; ++j) stage_sea(rp + (uint32_t)j * stride, (uint32_t)j);
+  }
   uint32_t join_local = 0;
   bool stop = false;
-  for (uint32_t rp = blockIdx.x * kDetectWarps + warp; rp < n_sea && !stop; rp += gridDim.x * kDetectWarps) {
-    // warp-uniform: lane 0 reads the flag, every lane sees its value
-    uint32_t ov = lane == 0 ? *reinterpret_cast<volatile uint32_t*>(&f.status->overflow) : 0u;
-    ov = __shfl_sync(kFull, ov, 0);
-    if (ov & 2u) break;
+  for (uint32_t it = 0; rp < n_sea && !stop; rp += stride, ++it) {
+    // the join-bound flag (warp-uniform: lane 0 reads it, every lane sees its
+    // value) is read here and tested after this SEA, so the read overlaps the
+    // work; a warp stops at most one SEA later than the bound was hit
+    const uint32_t ov = lane == 0 ? *reinterpret_cast<volatile uint32_t*>(&f.status->overflow) : 0u;
     const uint8_t* sea = seav + (uint64_t)rp * d.sea_bytes;
+    if (staged) {
+      // the SEA kSeaRing - 1 ahead goes to the slot this warp read last
+      // (every lane passed the __syncwarp at the end of that iteration); then
+      // wait for this SEA's copy and make every lane's bytes visible
+      stage_sea(rp + (uint32_t)(kSeaRing - 1) * stride, (it + kSeaRing - 1) % kSeaRing);
+      cp_async_wait<kSeaRing - 1>();
+      __syncwarp();
+      sea = ring + (it % kSeaRing) * kStagedSea;
+    }
     // 1. hot SEs per row
     uint32_t cnt[8];
     bool empty = false;
@@ -244,7 +282,10 @@ k_detect(DevParams d, const uint8_t* __restrict__ seav, LdcaRead ldca, const uin
         }
       }
       cnt[i] = n;
-      empty |= (n == 0);
+      if (n == 0) {                                  // no tuple can cover this row: the SEA yields nothing
+        empty = true;
+        break;
+      }
     }
     __syncwarp();
     if (!empty) {
@@ -304,8 +345,10 @@ k_detect(DevParams d, const uint8_t* __restrict__ seav, LdcaRead ldca, const uin
     __syncwarp();
     if (lane == 0) *queue_n = 0;
     __syncwarp();
-    stop = __any_sync(kFull, stop);
+    const bool bound = (__shfl_sync(kFull, ov, 0) & 2u) != 0u;
+    stop = __any_sync(kFull, stop) || bound;
   }
+  if (staged) cp_async_wait<0>();                  // no copy in flight at exit
   if (join_local) atomicAdd(reinterpret_cast<unsigned long long*>(&f.status->join), (unsigned long long)join_local);
 }
 
@@ -422,8 +465,11 @@ template <bool kSliding>
 cudaError_t detect_launch(const DevParams& d, const uint8_t* seav, const LdcaRead& ldca, const uint64_t* clock,
                           uint32_t k_slices, uint32_t z_theta, uint64_t* keys, uint32_t cap, uint64_t max_join,
                           DetectStatus* status, cudaStream_t s) {
+  // 512-byte SEAs of a 16-byte aligned SEAV are staged in shared memory
+  const bool staged = d.sea_bytes == kStagedSea && ((uintptr_t)seav & 15u) == 0u;
   const size_t smem = (size_t)kDetectWarps * kHostQueue * sizeof(uint32_t) +
-                      (size_t)kDetectWarps * d.sea_bytes * sizeof(uint16_t);
+                      (size_t)kDetectWarps * d.sea_bytes * sizeof(uint16_t) +
+                      (staged ? (size_t)kDetectWarps * kSeaRing * kStagedSea : 0u);
   cudaError_t e = cudaFuncSetAttribute(k_detect<kSliding>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -435,7 +481,7 @@ cudaError_t detect_launch(const DevParams& d, const uint8_t* seav, const LdcaRea
   uint64_t grid = (n_sea + kDetectWarps - 1) / kDetectWarps;
   if (grid > (uint64_t)sms * per_sm) grid = (uint64_t)sms * per_sm;
   Found f{keys, cap, max_join, status};
-  k_detect<kSliding><<<(unsigned)grid, kDetectThreads, smem, s>>>(d, seav, ldca, clock, k_slices, z_theta, f);
+  k_detect<kSliding><<<(unsigned)grid, kDetectThreads, smem, s>>>(d, seav, ldca, clock, k_slices, z_theta, f, staged);
   return cudaGetLastError();
 }
 

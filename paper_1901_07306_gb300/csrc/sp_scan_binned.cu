@@ -427,14 +427,24 @@ k_apply(DevParams d, const uint32_t* __restrict__ lists, const uint32_t* __restr
 }
 
 // 32 x 32 bit transpose across a warp: lane l holds row l (bit j = column j);
-// afterwards lane l holds column l (bit p = row p's bit l).
+// afterwards lane l holds column l (bit p = row p's bit l).  Stage s = 16, 8,
+// 4, 2, 1 swaps s x s blocks between lanes l and l ^ s.  With m the columns
+// whose bit s is clear, the lane whose bit s is clear keeps its m columns and
+// takes the partner's m columns moved up by s; the other lane keeps its ~m
+// columns and takes the partner's ~m columns moved down by s.  Either move is
+// a rotation of the partner's word (left by s, or by 32 - s) whose other bits
+// land in the columns the lane keeps, so a stage is one shuffle, one
+// funnel-shift rotation and one bitwise select.
 __device__ __forceinline__ uint32_t transpose32(uint32_t x, uint32_t lane) {
   const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
 #pragma unroll
   for (int st = 0; st < 5; ++st) {
-    const uint32_t s = 16u >> st, m = masks[st];
+    const uint32_t s = 16u >> st;
+    const bool high = (lane & s) != 0u;
+    const uint32_t keep = high ? ~masks[st] : masks[st];
     const uint32_t y = __shfl_xor_sync(kFull, x, s);
-    x = (lane & s) ? (((y >> s) & m) | (x & ~m)) : ((x & m) | ((y & m) << s));
+    const uint32_t t = __funnelshift_l(y, y, high ? 32u - s : s);
+    x = (x & keep) | (t & ~keep);
   }
   return x;
 }
