@@ -89,3 +89,38 @@ def test_request_larger_than_the_budget_is_refused():
     srv = S.SketchServer(1, budget_bytes=64 * 8 - 4, ops=FakeOps())
     with pytest.raises(ValueError):
         srv.run(_requests(1, size=64))
+
+
+class JitterOps(FakeOps):
+    """Device events that complete after a random number of polls."""
+
+    def __init__(self, seed):
+        super().__init__()
+        self.rng = np.random.default_rng(seed)
+
+    def issue_step(self, step):
+        self.steps.append([id(r) for r in step])
+        return FakeEvent(int(self.rng.integers(0, 40)))
+
+    def close_window(self):
+        i = len(self.windows)
+        self.windows.append(i)
+        return FakeEvent(int(self.rng.integers(0, 40))), i
+
+
+def test_windows_depend_only_on_arrival_order():
+    """How fast the device completes steps changes how requests are grouped
+    into steps, never which window a request belongs to or the windows'
+    pair counts (a window closes after detect_every admitted pairs)."""
+    sizes = np.random.default_rng(5).integers(16, 200, 60)
+    runs = []
+    for seed in range(4):
+        reqs = [S.Request(router=i % 5, pairs=torch.zeros(2 * int(n), dtype=torch.int32), arrival=0.0)
+                for i, n in enumerate(sizes)]
+        srv = S.SketchServer(5, budget_bytes=8 * 400, detect_every=1000, max_step_requests=3,
+                             ops=JitterOps(seed))
+        wins = srv.run(reqs)
+        runs.append(([r.window for r in reqs], [w.n_pairs for w in wins]))
+    assert all(r == runs[0] for r in runs[1:])
+    windows, pairs = runs[0]
+    assert sum(pairs) == int(sizes.sum()) and all(p >= 1000 for p in pairs[:-1])
