@@ -156,6 +156,21 @@ def test_single_pair_sets_expected_bits():
     assert int(np.unpackbits(s.ldca.view(np.uint8)).sum()) == 3
 
 
+def test_sampling_boundary_is_inclusive():
+    """Sec. 3.1 (reading 2: lsb(H1(oip)) >= tau): a pair whose H1 has its
+    lowest set bit exactly at tau is sampled -- its SE bit is set in every
+    SEA row -- and one whose lowest set bit is at tau - 1 is not."""
+    p = O.Params(**dict(TINY, theta=64))            # tau = 3
+    tau = O.tau(p.theta)
+    assert tau == 3
+    at = next(o for o in range(1, 1 << 20) if O.lsb(O.h1(p, o)) == tau)
+    below = next(o for o in range(1, 1 << 20) if O.lsb(O.h1(p, o)) == tau - 1)
+    for oip, sampled in ((at, True), (below, False)):
+        s = _sketch(np.array([[0x0A0B0C0D, oip]], np.uint32), **dict(TINY, theta=64))
+        assert int(np.unpackbits(s.seav).sum()) == (p.sr if sampled else 0), oip
+        assert int(np.unpackbits(s.ldca.view(np.uint8)).sum()) == p.lr   # the LDCA takes every pair
+
+
 def test_sampling_rate_matches_tau():
     # lsb(H1(oip)) >= tau happens with probability 2^-tau for a uniform H1
     p = O.Params(**dict(TINY, theta=64))  # tau = 3
@@ -271,6 +286,41 @@ def test_detect_matches_forward_brute_force(seed):
     assert {int(c["ip"]): int(c["z0"]) for c in got} == expect
     assert list(got["ip"]) == sorted(got["ip"])
     assert len(set(heavy) & set(expect)) >= 6
+
+
+def test_threshold_boundary_is_inclusive():
+    """Def. 2 and Eq. 4 (reading 11: Est >= theta as z0 <= Z_theta): one host
+    alone in the stream has a ULDC of exactly k - |H3(peers)| zeros (no other
+    host shares its LDCs).  With Z_theta = floor(k exp(-theta / k)) zeros it
+    is reported; with one zero more it is not."""
+    theta, k = 64, 256
+    p = O.Params(**dict(TINY, theta=theta, seed=77))
+    zt = math.floor(k * math.exp(-theta / k))       # 199
+    host = 0x0A0B0C0D
+
+    def peers_with_distinct_h3(d):
+        seen, peers, o = set(), [], 1
+        while len(seen) < d:
+            h = O.h3(p, o)
+            if h not in seen:
+                seen.add(h)
+                peers.append(o)
+            o += 1
+        # enough sampled peers with distinct H2 for a hot SE in every row,
+        # taken among peers whose H3 is already present (z0 unchanged)
+        bits = {O.h1(p, x) >> 29 for x in peers if O.lsb(O.h1(p, x)) >= O.tau(theta)}
+        while len(bits) < 3:
+            h1 = O.h1(p, o)
+            if O.h3(p, o) in seen and O.lsb(h1) >= O.tau(theta) and (h1 >> 29) not in bits:
+                bits.add(h1 >> 29)
+                peers.append(o)
+            o += 1
+        return np.stack([np.full(len(peers), host, np.uint32), np.array(peers, np.uint32)], 1)
+
+    got, n, _ = O.Sketch(p).update(peers_with_distinct_h3(k - zt)).detect(theta)
+    assert n == 1 and int(got["ip"][0]) == host and int(got["z0"][0]) == zt
+    got, n, _ = O.Sketch(p).update(peers_with_distinct_h3(k - zt - 1)).detect(theta)
+    assert n == 0
 
 
 def test_detect_reports_est_and_saturation():
