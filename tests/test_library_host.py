@@ -130,3 +130,28 @@ def test_bounds_probe_library_exports_its_header():
     lib = ctypes.CDLL(build.BOUNDS_LIB)
     for name in names:
         assert hasattr(lib, name), name
+
+
+def test_param_validation_agrees_with_oracle_on_random_profiles(sp):
+    """The library's and the oracle's checks of the Sec. 3.2 constraints
+    (coverage, cyclic overlap of consecutive rows) are written independently;
+    on random SEAV profiles inside the library's limits they accept and
+    reject the same sets."""
+    import numpy as np
+    import oracle as O
+    rng = np.random.default_rng(123)
+    accepted = rejected = 0
+    for _ in range(3000):
+        r = int(rng.integers(0, 25))
+        L = 32 - r
+        sr = int(rng.integers(1, 9))
+        ibn = tuple(int(x) for x in rng.integers(1, min(12, L) + 1, sr))
+        isb = tuple(int(x) for x in rng.integers(0, L, sr))
+        if sum(1 << b for b in ibn) > 4096:                 # a library limit, not a paper constraint
+            continue
+        want = O.check_params(O.Params(r=r, isb=isb, ibn=ibn)) == 0
+        got = sp.sp_check_params(sp.make_params(r=r, isb=isb, ibn=ibn)) == 0
+        assert got == want, (r, isb, ibn)
+        accepted += want
+        rejected += not want
+    assert accepted > 100 and rejected > 100
